@@ -1,0 +1,109 @@
+"""Pins of the oracle's fluctuating-LB noise (Sec. 4, Eqs. NP1-NP2, Table 1)."""
+import os
+
+import numpy as np
+import pytest
+
+
+def _triton_philox(keys, ctrs):
+    """Philox4x32-10 from triton's own implementation, run by its CPU interpreter."""
+    os.environ["TRITON_INTERPRET"] = "1"
+    torch = pytest.importorskip("torch")
+    triton = pytest.importorskip("triton")
+    import triton.language as tl
+
+    @triton.jit
+    def kern(out_ptr, c_ptr, seed, N: tl.constexpr):
+        offs = tl.arange(0, N)
+        c0 = tl.load(c_ptr + offs * 4 + 0)
+        c1 = tl.load(c_ptr + offs * 4 + 1)
+        c2 = tl.load(c_ptr + offs * 4 + 2)
+        c3 = tl.load(c_ptr + offs * 4 + 3)
+        a, b, c, d = tl.philox(seed, c0, c1, c2, c3, 10)
+        tl.store(out_ptr + offs * 4 + 0, a)
+        tl.store(out_ptr + offs * 4 + 1, b)
+        tl.store(out_ptr + offs * 4 + 2, c)
+        tl.store(out_ptr + offs * 4 + 3, d)
+
+    res = []
+    for key in keys:
+        seed = int(key[0]) | (int(key[1]) << 32)
+        c = torch.tensor(np.asarray(ctrs, dtype=np.uint32).view(np.int32).reshape(-1))
+        out = torch.zeros_like(c)
+        kern[(1,)](out, c, seed, len(ctrs))
+        res.append(out.numpy().view(np.uint32).reshape(-1, 4))
+    return res
+
+
+def test_philox_matches_independent_implementation(oracle):
+    """Philox4x32-10 (Salmon et al., SC'11): the oracle's words equal triton's."""
+    rng = np.random.default_rng(11)
+    ctrs = rng.integers(0, 2 ** 32, size=(16, 4), dtype=np.uint64).astype(np.uint32)
+    ctrs[0] = 0
+    ctrs[1] = 0xFFFFFFFF
+    keys = [(0, 0), (0xFFFFFFFF, 0xFFFFFFFF), (0x12345678, 0x9ABCDEF0)]
+    try:
+        ref = _triton_philox(keys, ctrs)
+    except Exception as exc:  # pragma: no cover - interpreter unavailable
+        pytest.skip(f"triton CPU interpreter unavailable: {exc}")
+    for key, r in zip(keys, ref):
+        for c, expect in zip(ctrs, r):
+            assert np.array_equal(oracle.philox(c, key), expect)
+
+
+def test_box_muller_normals_statistics(oracle):
+    """Theta_k are standard normal deviates (Sec. 4): moments and independence."""
+    z = np.array([oracle.thetas(20061291, node, step) for node in range(4000) for step in range(5)])
+    flat = z.reshape(-1)
+    n = flat.size
+    assert abs(flat.mean()) < 5 / np.sqrt(n)
+    assert abs(flat.var() - 1) < 5 * np.sqrt(2 / n)
+    assert abs((flat ** 4).mean() - 3) < 5 * np.sqrt(96 / n)
+    c = np.corrcoef(z.T)
+    assert np.abs(c - np.eye(6)).max() < 5 / np.sqrt(z.shape[0])
+
+
+def test_philox_uniform_chi_square(oracle):
+    words = np.array([oracle.philox([i, 7, 0, 3], [99, 1]) for i in range(20000)]).reshape(-1)
+    counts = np.bincount((words >> 24).astype(np.int64), minlength=256)
+    exp = words.size / 256
+    chi2 = ((counts - exp) ** 2 / exp).sum()
+    assert chi2 < 255 + 6 * np.sqrt(2 * 255)
+
+
+def test_noise_conserves_mass_and_momentum_and_hits_modes(oracle):
+    """Eq. NP2 acts only on modes 3..8: sum zeta = sum zeta e = 0, and the
+    projection on mode k is the amplitude times Theta_k."""
+    e, w, _ = oracle.lattice()
+    chi, _ = oracle.basis()
+    rng = np.random.default_rng(12)
+    for _ in range(10):
+        th = rng.standard_normal(6)
+        rho, kT, om = 1.0 + 0.01 * rng.standard_normal(), 1e-4, 1 / rng.uniform(0.6, 1.5)
+        z = oracle.noise(rho, kT, om, th)
+        amp = np.sqrt(rho * kT * om * (2 - om) * 3.0)
+        tol = 1e-14 * np.abs(z).max()
+        assert abs(z.sum()) < tol
+        assert np.abs(z @ e).max() < tol
+        m = chi @ z
+        assert np.abs(m[:3]).max() < tol
+        assert np.allclose(m[3:], amp * th, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_equipartition_of_every_mode(oracle, tau):
+    """Thermalised FLB (Sec. 4; Duenweg, Schiller & Ladd 2007): each mode k of the
+    fluctuation carries <m_k^2> = rho kT / c_s^2; for the momentum this is
+    <j_x^2> = <j_y^2> = rho kT and for the density <drho^2> = rho kT / c_s^2."""
+    N, kT = 32, 1e-4
+    chi, _ = oracle.basis()
+    d = oracle.Domain(oracle.make_params(nx=N, ny=N, tau=tau, kT=kT, seed=1234))
+    d.step(500)
+    acc = []
+    for _ in range(400):
+        d.step(10)
+        f = d.populations().reshape(9, -1)
+        m = chi @ f
+        acc.append(np.concatenate([[((f.sum(0) - 1) ** 2).mean()], (m[1:] ** 2).mean(1)]))
+    ratio = np.mean(acc, axis=0) / (3 * kT)
+    assert np.abs(ratio - 1).max() < 0.02

@@ -1,0 +1,91 @@
+"""Pins of the oracle's power-law relaxation time (Sec. 5, Eqs. nn1-nn7)."""
+import numpy as np
+import pytest
+from scipy.optimize import brentq
+
+
+@pytest.mark.parametrize("n", [0.5, 0.75, 1.5, 3.0])
+@pytest.mark.parametrize("A", [1e-5, 3e-3, 0.05])
+def test_tau_root_matches_library_root_finder(oracle, n, A):
+    """tau* = 1/2 + 3 xi (A / tau*)^(n-1) (nn4 with kappa = 2^(n-1)), clamped."""
+    xi, tmin, tmax = 0.01, 0.51, 2.0
+    t = oracle.solve_tau(A, n, xi, tmin, tmax)
+
+    def g(s):
+        return s - 0.5 - 3 * xi * (A / s) ** (n - 1)
+
+    if g(tmin) >= 0:
+        assert t == tmin
+    elif g(tmax) <= 0:
+        assert t == tmax
+    else:
+        ref = brentq(g, tmin, tmax, xtol=1e-15, rtol=1e-15)
+        assert t == pytest.approx(ref, rel=1e-13)
+        assert abs(g(t)) < 1e-14
+
+
+def test_tau_limits_at_zero_strain(oracle):
+    """Sec. 5: nu* -> infinity (n<1) or 0 (n>1) at zero strain; the clamp holds."""
+    assert oracle.solve_tau(0.0, 0.5, 0.01, 0.51, 2.0) == 2.0
+    assert oracle.solve_tau(0.0, 1.5, 0.01, 0.51, 2.0) == 0.51
+    assert oracle.solve_tau(0.3, 1.0, 0.1, 0.51, 2.0) == pytest.approx(0.8, rel=1e-15)
+
+
+def test_strain_invariant_matches_nn3(oracle):
+    """2 sqrt|Pi_D| with Pi_D from Eq. nn3, the velocity gradients taken as the
+    Chapman-Enskog strain S = -Pi_neq / (2 rho c_s^2 tau), equals A / tau."""
+    rng = np.random.default_rng(7)
+    e, w, _ = oracle.lattice()
+    e = e.astype(float)
+    for _ in range(20):
+        f = w * (1 + 0.05 * rng.standard_normal(9))
+        rho = f.sum()
+        j = f @ e
+        tau = rng.uniform(0.55, 1.9)
+        Pi = np.einsum("i,ia,ib->ab", f, e, e) - rho / 3 * np.eye(2) - np.outer(j, j) / rho
+        S = -Pi / (2 * rho / 3 * tau)
+        ux, vy = S[0, 0], S[1, 1]
+        uy_plus_vx = 2 * S[0, 1]
+        PiD = 0.25 * uy_plus_vx ** 2 - ux * vy
+        A = oracle.strain_A(f, rho, j[0], j[1])
+        assert 2 * np.sqrt(abs(PiD)) == pytest.approx(A / tau, rel=1e-12)
+
+
+def test_newtonian_limit_is_bgk(oracle):
+    """n = 1 gives nu* = xi, i.e. plain BGK with tau = 1/2 + 3 xi, bit for bit."""
+    rng = np.random.default_rng(8)
+    _, w, _ = oracle.lattice()
+    nx, ny = 20, 12
+    f0 = w[:, None, None] * (1 + 0.01 * rng.standard_normal((9, ny, nx)))
+    base = dict(nx=nx, ny=ny, periodic_x=1, periodic_y=0, walls_y=1, gx=1e-5)
+    a = oracle.Domain(oracle.make_params(tau=0.8, **base), f0=f0)
+    b = oracle.Domain(oracle.make_params(tau=9.0, power_law=1, n_pl=1.0, xi_pl=0.1,
+                                         tau_min=0.51, tau_max=2.0, **base), f0=f0)
+    a.step(50)
+    b.step(50)
+    assert np.abs(a.populations() - b.populations()).max() < 1e-16
+
+
+@pytest.mark.parametrize("n,xi,g", [(0.5, 1e-3, 3.9e-6), (0.75, 0.02, 2e-5), (1.5, 2.2, 1.3e-5)])
+def test_channel_profile_matches_nn6_nn7(oracle, n, xi, g):
+    """Steady gravity-driven channel of width W: u(y) = u0 [1 - (2|y|/W)^(1+1/n)],
+    u0 = (g/xi)^(1/n) (W/2)^(1+1/n) n/(n+1) (Eqs. nn6-nn7, y from the centreline),
+    with the clamp inactive away from the centreline at these settings."""
+    W, nx = 32, 4
+    u0 = (g / xi) ** (1 / n) * (W / 2) ** (1 + 1 / n) * n / (n + 1)
+    Yc = np.abs(np.arange(W) + 0.5 - W / 2)
+    prof0 = u0 * (1 - (2 * Yc / W) ** (1 + 1 / n))
+    f0 = np.zeros((9, W, nx))
+    for y in range(W):
+        f0[:, y, :] = oracle.feq(1.0, 0.98 * prof0[y], 0.0)[:, None]
+    p = oracle.make_params(nx=nx, ny=W, periodic_x=1, periodic_y=0, walls_y=1, tau=1.0, gx=g,
+                           power_law=1, n_pl=n, xi_pl=xi, tau_min=0.51, tau_max=2.0)
+    d = oracle.Domain(p, f0=f0)
+    last = None
+    for _ in range(100):
+        d.step(2000)
+        prof = d.moments()[1][:, 0]
+        if last is not None and np.abs(prof - last).max() < 1e-9 * prof.max():
+            break
+        last = prof.copy()
+    assert np.abs(prof - prof0).max() / u0 < 1e-2
