@@ -168,8 +168,10 @@ void or_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* 24-bit uniform in (0,1): exactly representable in FP32 and FP64. */
-static double u24(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
+/* Uniform in (0,1) from the top 23 bits: ((x >> 9) + 1/2) / 2^23 is an odd
+ * multiple of 2^-24 below 1, exactly representable in FP32 and FP64, so every
+ * implementation of the generator draws the identical uniform. */
+static double u23(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 /* Six standard normal deviates Theta_3..Theta_8 of Eq. (NP2) for one node and
  * step.  Counter = (node, step, draw, domain), key = (seed_lo, seed_hi); draw 0
@@ -183,7 +185,7 @@ void or_thetas(uint64_t seed, uint32_t node, uint32_t step, uint32_t domain, dou
     }
     const double two_pi = 6.283185307179586476925286766559;
     for (int pr = 0; pr < 3; ++pr) {
-        const double ua = u24(r[2 * pr]), ub = u24(r[2 * pr + 1]);
+        const double ua = u23(r[2 * pr]), ub = u23(r[2 * pr + 1]);
         const double rad = sqrt(-2.0 * log(ua));
         th[2 * pr] = rad * cos(two_pi * ub);
         th[2 * pr + 1] = rad * sin(two_pi * ub);
