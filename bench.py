@@ -1,0 +1,351 @@
+"""Benchmark of the D2Q9 hot path on GB300: MLUPS of the porous-medium workload.
+
+Workload (one step = one full timestep of the hot path over the whole domain):
+2048x1024 D2Q9 lattice, ~300 seeded disk obstacles R~U[8,24] (gap >= 4),
+20 free disk particles R=10 with rho_p/rho = 1.05 (Ladd moving bounce-back,
+momentum-exchange force, covered/uncovered nodes, LJ repulsion, FP64
+Newton-Euler), Zou-He density ends 1.001 / 0.999, halfway walls in y, tau=0.7,
+FP32 arithmetic on shifted FP32 storage.  MLUPS = nodes * steps / (1e6 s),
+counting every node as the paper does (Sec. 7).
+
+Prints ONE JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 MLUPS and % HBM roofline, FP32/FP16-store vs FP64 path at stated error"
+UNIT = "MLUPS"
+STORE_BYTES = {"f64": 8, "f32": 4, "f32s": 4, "f16s": 2, "bf16s": 2}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            j = json.load(fh)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"lbm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) >= 9:
+                    rows.append(c)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        mx = max(num(r[2]) for r in rows)
+        pw = [num(r[3]) for r in rows]
+        pmax = max(p for p in pw if p == p) if any(p == p for p in pw) else 0.0
+        load = [s for s, p in zip(sm, pw) if p == p and p >= 0.5 * pmax] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": pmax}
+
+
+def porous_workload(nx=2048, ny=1024):
+    from paper_2006_12910_gb300 import workloads
+    return workloads.porous(nx, ny)
+
+
+def cpu_oracle_mlups(w, budget_s: float, steps_hint: int | None = None):
+    """Time the FP64 oracle, as it stands, on the host cores for ~budget_s."""
+    from oracle import oracle
+    oracle.build()
+    p = oracle.make_params(nx=w.nx, ny=w.ny, **{k: v for k, v in w.params.items()
+                                                 if k in {f[0] for f in oracle.Params._fields_}})
+    d = oracle.Domain(p, solid=w.solid, particles=w.particles)
+    t0 = time.perf_counter()
+    d.step(1)
+    t1 = time.perf_counter()
+    per = max(t1 - t0, 1e-6)
+    n = steps_hint or max(1, int(budget_s / per))
+    t0 = time.perf_counter()
+    d.step(n)
+    t = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return w.nx * w.ny * n / t / 1e6, n, t, cores
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    # Each reference step is one oracle timestep over a scaled-down sample of the
+    # porous workload, sized so that warmup + steps fit in about two minutes.
+    from paper_2006_12910_gb300 import workloads
+    total_steps = args.steps + args.warmup
+    probe = workloads.porous(512, 256)
+    from oracle import oracle
+    oracle.build()
+    pp = oracle.make_params(nx=probe.nx, ny=probe.ny, **{k: v for k, v in probe.params.items()
+                                                         if k in {f[0] for f in oracle.Params._fields_}})
+    dprobe = oracle.Domain(pp, solid=probe.solid, particles=probe.particles)
+    t0 = time.perf_counter()
+    dprobe.step(2)
+    rate = probe.nx * probe.ny * 2 / max(time.perf_counter() - t0, 1e-6)  # node updates per second
+    budget = 100.0
+    nodes = max(64 * 64, min(2048 * 1024, int(rate * budget / max(total_steps, 1))))
+    ny = int(max(32, min(1024, round((nodes / 2) ** 0.5 / 8) * 8)))
+    nx = int(max(64, min(2048, round(nodes / ny / 8) * 8)))
+    w = workloads.porous(nx, ny)
+    p = oracle.make_params(nx=w.nx, ny=w.ny, **{k: v for k, v in w.params.items()
+                                                 if k in {f[0] for f in oracle.Params._fields_}})
+    d = oracle.Domain(p, solid=w.solid, particles=w.particles)
+    d.step(args.warmup)
+    t0 = time.perf_counter()
+    d.step(args.steps)
+    t = time.perf_counter() - t0
+    value = w.nx * w.ny * args.steps / t / 1e6
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = (f"{w.nx}x{w.ny} sample of the porous workload ({w.note}), FP64 oracle, "
+              f"{args.steps} timed steps after {args.warmup} warm-up")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"porous {w.nx}x{w.ny} (sample of porous 2048x1024)", "nodes": w.nx * w.ny,
+                       "store": "f64 (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--store", default="f32s", choices=list(STORE_BYTES))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2000)
+    ap.add_argument("--profile-steps", type=int, default=500)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--nx", type=int, default=2048)
+    ap.add_argument("--ny", type=int, default=1024)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2006_12910_gb300 import lbm
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+
+    w = porous_workload(args.nx, args.ny)
+    nodes = w.nx * w.ny
+    fluid = int((w.solid == 0).sum())
+    base = {k: v for k, v in w.params.items()}
+    scale = 4096.0 if args.store in ("f16s", "bf16s") else 1.0
+
+    def make_ctx(store):
+        p = lbm.make_params(nx=w.nx, ny=w.ny, store=store, max_particles=len(w.particles), store_scale=scale, **base)
+        return lbm.Context(p, stream=stream.cuda_stream, solids=[w.solid], particles=[w.particles])
+
+    ctx = make_ctx(args.store)
+    if not args.no_autotune:
+        ctx.autotune(20)
+    kernels_per_step = 3 if w.particles else 1
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- device-timed region: W warm-up steps, then exactly K steps ----------------------
+    ctx.step(args.warmup)
+    ctx.sync()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").strip()
+    smi_index = vis.split(",")[dev] if vis else str(dev)
+    clocks = ClockSampler(smi_index)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ctx.sync()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nodes * args.steps / (ms * 1e-3) / 1e6
+
+    # ---- per-kernel device time (CUDA events around each launch on the same stream) ------
+    kf, kl, kk, nl = ctx.profile_steps(args.profile_steps)
+    k1_ms = kk / args.profile_steps
+    S = STORE_BYTES[args.store]
+    alg_bytes = fluid * 2 * 9 * S  # read 9 + write 9 populations per fluid node update
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / (k1_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_stream_collide", "peak_source": peak_kind,
+                "alg_bytes_per_launch": alg_bytes, "kernel_ms": k1_ms,
+                "kernel_share": kk / max(kf + kl + kk, 1e-9),
+                "particle_kernels_ms": [kf / args.profile_steps, kl / args.profile_steps]}
+
+    # ---- end to end through the C ABI with host buffers ------------------------------------
+    # Upload the initial state from pinned host memory, then every step: advance and read
+    # the particle state back to the host; finally read the moment fields back.
+    e2e = None
+    if rank == 0 or world > 1:
+        ctx2 = make_ctx(args.store)
+        f0 = torch.empty((9, w.ny, w.nx), dtype=torch.float64, pin_memory=True)
+        f0.numpy()[:] = ctx2.populations()
+        K2 = args.e2e_steps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx2.set_populations(f0.numpy())
+        for _ in range(K2):
+            ctx2.step(1)
+            ctx2.particles()
+        rho, ux, uy = ctx2.moments()
+        t = time.perf_counter() - t0
+        h2d = 9 * nodes * 8 / K2
+        d2h = len(w.particles) * 64 + 3 * nodes * 8 / K2
+        e2e = {"value": world * nodes * K2 / t / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": K2,
+               "what": "lbm_set_populations(pinned FP64) + K x [lbm_step(1) + lbm_particles] + lbm_moments"}
+        ctx2.close()
+
+    # ---- other storage kinds on the same workload (short) ----------------------------------
+    variants = {}
+    if not args.no_variants and rank == 0:
+        for store in ("f16s", "f64"):
+            if store == args.store:
+                continue
+            scale = 4096.0 if store in ("f16s", "bf16s") else 1.0
+            c3 = make_ctx(store)
+            if not args.no_autotune:
+                c3.autotune(10)
+            n3 = 2000 if store != "f64" else 500
+            c3.step(50)
+            c3.sync()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            c3.step(n3)
+            a1.record(stream)
+            a1.synchronize()
+            c3.sync()
+            m3 = a0.elapsed_time(a1)
+            _, _, k3, _ = c3.profile_steps(100)
+            b3 = fluid * 2 * 9 * STORE_BYTES[store]
+            variants[store] = {"MLUPS": nodes * n3 / (m3 * 1e-3) / 1e6,
+                               "kernel_GBs": b3 / (k3 / 100 * 1e-3) / 1e9,
+                               "frac": b3 / (k3 / 100 * 1e-3) / 1e9 / peak}
+            c3.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, n, t, cores = cpu_oracle_mlups(w, budget_s=15.0)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} timesteps of the full 2048x1024 porous workload, FP64 oracle, OpenMP static"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"porous {w.nx}x{w.ny} D2Q9: {w.note}, tau=0.7, walls y",
+                           "nodes": nodes, "fluid_nodes": fluid, "store": args.store,
+                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                           "l2": "no flush; per-step footprint (2 arenas) exceeds the 129 MB L2",
+                           "launch": {"block": None, "graph_steps": 8}},
+                "clocks": clk, "gpu_launches": args.steps * kernels_per_step,
+                "roofline": roofline, "e2e": e2e, "variants": variants, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * lbm.h -- C ABI of the GB300 D2Q9 lattice Boltzmann library.
+ *
+ * What it computes: the per-timestep hot path of the 2-D lattice Boltzmann
+ * model of arXiv:2006.12910 (Basagaoglu, Harwell, Nguyen & Succi):
+ *   - D2Q9 single-relaxation BGK with a velocity-shift body force
+ *     (Sec. 2, Eqs. e.LB1, e.LB2, rho u = sum f e + tau rho g);
+ *   - halfway bounce-back at walls and stationary obstacles (Sec. 3);
+ *   - Ladd moving bounce-back on circular particles with the momentum-exchange
+ *     force, covered/uncovered-node force, LJ-type repulsion and a Newton-Euler
+ *     update (Sec. 3, Eqs. MP1-MP8);
+ *   - fluctuating-LB thermal noise on modes 3..8 (Sec. 4, Eqs. NP1-NP2,
+ *     Table 1), from a counter-based Philox4x32-10 stream keyed on
+ *     (seed, node, step, draw, domain) so that no random state is stored;
+ *   - a local power-law relaxation time tau* (Sec. 5, Eqs. nn1-nn5);
+ *   - Zou-He density columns at the x ends (an addition: the paper's
+ *     benchmark 1 uses periodic ends with a body force).
+ * Every step runs in hand-written CUDA kernels for sm_103a; there is no CPU
+ * fallback.  All device memory is owned by the context.
+ *
+ * Conventions for every call:
+ *   - Return value: LBM_OK (0) or a negative LBM_E_* code; no exception ever
+ *     crosses this interface.  lbm_last_error() gives a one-line reason.
+ *   - Host arrays passed in are copied before the call returns; output arrays
+ *     are allocated by the caller.
+ *   - Field layout on the host: x fastest, rows of nx values, ny rows
+ *     (index y*nx + x); populations as [9][ny][nx] with the paper's velocity
+ *     order e0=(0,0), e1..e4 = (1,0),(0,1),(-1,0),(0,-1),
+ *     e5..e8 = (1,1),(-1,1),(-1,-1),(1,-1) (Sec. 2).
+ *   - The stored state is the POST-collision populations f*(t): one step
+ *     streams them with bounce-back and collides (the paper's collide-then-
+ *     stream sequence shifted by half a step).
+ *   - lbm_step enqueues work on the context's stream and returns; errors that
+ *     arise on the device (instability, particle overlap, a bounded wait
+ *     running out) are reported by the next blocking call.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_E_INVAL (-1)    /* bad argument or parameter */
+#define LBM_E_NOMEM (-2)    /* device or pinned allocation failed */
+#define LBM_E_CUDA (-3)     /* a CUDA runtime call failed */
+#define LBM_E_UNSTABLE (-4) /* NaN / Inf or rho <= 0 seen on the lattice */
+#define LBM_E_TIMEOUT (-5)  /* a bounded device-side wait ran out */
+#define LBM_E_STATE (-6)    /* call order, particle overlap or list capacity */
+#define LBM_E_IO (-7)       /* checkpoint file error */
+
+/* Population storage.  F64 stores f and computes in FP64 (the plain FP64
+ * path).  Every other kind computes in FP32 registers: F32 stores f, the
+ * shifted kinds store (f_i - omega_i rho0) * store_scale. */
+typedef enum {
+    LBM_F64 = 0,
+    LBM_F32 = 1,
+    LBM_F32S = 2,
+    LBM_F16S = 3,
+    LBM_BF16S = 4
+} lbm_store;
+
+/* One lattice domain.  Lattice units, dx = dt = 1 (Sec. 6). */
+typedef struct {
+    int32_t nx, ny;            /* nodes; nx, ny >= 3 */
+    int32_t periodic_x;        /* exactly one of periodic_x / inlet_outlet */
+    int32_t periodic_y;        /* exactly one of periodic_y / walls_y */
+    int32_t walls_y;           /* halfway walls at y = -1/2 and y = ny - 1/2 */
+    int32_t inlet_outlet;      /* Zou-He density columns at x = 0 and x = nx-1 */
+    double tau;                /* BGK relaxation time (> 1/2); nu = (tau - 1/2)/3 */
+    double rho0;               /* reference density (rest state, particle links) */
+    double gx, gy;             /* body-force acceleration g (Sec. 2) */
+    double rho_in, rho_out;    /* densities of the open columns */
+    double kT;                 /* thermal energy of Eq. NP2; 0 disables noise */
+    uint64_t seed;             /* Philox key */
+    uint32_t domain_id;        /* fourth Philox counter word */
+    int32_t power_law;         /* 1: tau* of Sec. 5 replaces tau */
+    double n_pl, xi_pl;        /* power-law index n and consistency xi (Eq. nn1) */
+    double tau_min, tau_max;   /* clamp of tau* */
+    double lj_psi, lj_rit;     /* Eq. MP2 stiffness psi and threshold |r_it| */
+    int32_t store;             /* lbm_store; must be the same for every domain */
+    int32_t max_particles;     /* capacity reserved for lbm_add_particles */
+    double store_scale;        /* power-of-two scale of the shifted FP16/BF16 store */
+} lbm_params;
+
+/* A rigid circular particle (Sec. 3).  Position in lattice units with node
+ * (x, y) at integer coordinates; velocity U, V; angular velocity Omega;
+ * orientation theta.  fixed = 1 holds position and velocity. */
+typedef struct {
+    double x, y, R, rho_p, U, V, Omega, theta;
+    int32_t fixed;
+    int32_t pad_;
+} lbm_particle;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Create a context for one domain (Sec. 2 parameters), allocate its device
+ * memory and set the state to the rest equilibrium f* = omega_i rho0.
+ * cuda_stream: a cudaStream_t the context enqueues on (NULL: the context
+ * creates its own).  On success *out owns everything until lbm_destroy. */
+int lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out);
+
+/* Create a context holding ndom independent domains of uneven size that
+ * advance together (one stream-and-collide launch per step over a work list
+ * covering all domains).  per_domain[d] describes domain d; store must agree. */
+int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_stream, lbm_ctx** out);
+
+/* Stationary solid nodes of domain dom (Sec. 3 "inline obstacles"):
+ * solid[y*nx + x] != 0 marks a solid node.  Copied.  Solid nodes hold no
+ * populations; their neighbours bounce back halfway.  Must precede
+ * lbm_add_particles. */
+int lbm_set_geometry(lbm_ctx* ctx, int dom, const uint8_t* solid);
+
+/* Add n particles to domain dom (copied) and rasterise them (Sec. 3, Fig. 1:
+ * a node belongs to a particle when strictly inside its disk).  Particles
+ * must not overlap each other.  Total per domain <= max_particles. */
+int lbm_add_particles(lbm_ctx* ctx, int dom, int n, const lbm_particle* p);
+
+/* Replace the populations f*(t) of domain dom with host FP64 values
+ * f[9][ny][nx] (converted to the store type; solid nodes ignored). */
+int lbm_set_populations(lbm_ctx* ctx, int dom, const double* f);
+
+/* Read the populations f*(t) of domain dom into host FP64 f[9][ny][nx]
+ * (solid nodes read as 0).  Blocking. */
+int lbm_get_populations(lbm_ctx* ctx, int dom, double* f);
+
+/* Advance every domain by nsteps timesteps (Eqs. e.LB1, MP1-MP8, NP1-NP2,
+ * nn5 per step).  Enqueued on the context stream (replayed as a CUDA graph);
+ * returns without waiting. */
+int lbm_step(lbm_ctx* ctx, int64_t nsteps);
+
+/* Wait for the context stream and report device-side errors. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* Density and physical velocity u = (sum f* e - rho g / 2) / rho of domain dom
+ * into caller host arrays of ny*nx doubles (solid nodes: 0).  Blocking. */
+int lbm_moments(lbm_ctx* ctx, int dom, double* rho, double* ux, double* uy);
+
+/* Same moments as FP32 into caller DEVICE arrays of ny*nx floats on the
+ * context stream (for example torch tensors).  Not blocking. */
+int lbm_moments_device(lbm_ctx* ctx, int dom, float* d_rho, float* d_ux, float* d_uy);
+
+/* Start an asynchronous copy of the moments of domain dom to pinned host
+ * memory on a side stream (output offloading); lbm_moments_async_wait copies
+ * them into the caller's host arrays (FP32, ny*nx each). */
+int lbm_moments_async(lbm_ctx* ctx, int dom);
+int lbm_moments_async_wait(lbm_ctx* ctx, float* rho, float* ux, float* uy);
+
+/* Particle state of domain dom at the current step (up to cap entries).
+ * Returns the particle count (>= 0) or an error. Blocking. */
+int lbm_particles(lbm_ctx* ctx, int dom, lbm_particle* out, int cap);
+
+/* Force and torque terms of the last step for particle i of domain dom, 13
+ * doubles: F_links(x,y), T_links (Eq. MP1), F_cu(x,y), T_cu (covered /
+ * uncovered nodes), F_lj(x,y), T_lj (Eq. MP2), n_covered, n_uncovered,
+ * mass_covered, mass_uncovered.  Blocking. */
+int lbm_particle_forces(lbm_ctx* ctx, int dom, int i, double* out13);
+
+/* FP64 global sums over fluid nodes of domain dom: mass sum f*, momentum
+ * sum f* e_x, sum f* e_y (deterministic block order).  Blocking. */
+int lbm_checks(lbm_ctx* ctx, int dom, double* out3);
+
+/* Steps completed since creation (or since the loaded checkpoint). */
+int64_t lbm_step_count(const lbm_ctx* ctx);
+
+/* Checkpoint: populations, particle state, rasterisation and step counter.
+ * Because the noise is counter-based, a resumed run is bit-identical. */
+int lbm_save(lbm_ctx* ctx, const char* path);
+int lbm_load(lbm_ctx* ctx, const char* path);
+
+/* Pick the stream-and-collide launch shape (warps per block, rows per warp
+ * item) by short timed trials on the context's own data; the state is saved
+ * and restored around the trials. */
+int lbm_autotune(lbm_ctx* ctx, int trial_steps);
+
+/* Measurement: advance nsteps timesteps with plain launches (no graph) and a
+ * CUDA-event pair around every kernel on the context stream; ms_out[0..2]
+ * receive the summed device time of the particle-force kernel, the
+ * link-exchange kernel and the stream-and-collide kernel, and launches_out
+ * (if not NULL) the number of kernels launched.  Blocking.  The state
+ * advances exactly as with lbm_step. */
+int lbm_profile_steps(lbm_ctx* ctx, int64_t nsteps, double* ms_out3, int64_t* launches_out);
+
+/* Last error message of the context (static string when ctx is NULL). */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Release the context and all of its device memory. */
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_GB300_H */

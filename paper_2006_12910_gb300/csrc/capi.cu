@@ -1,0 +1,915 @@
+// capi.cu -- host runtime and C ABI of the GB300 D2Q9 library (include/lbm.h).
+//
+// The context owns every device buffer: two population arenas (the state
+// f*(t) and the next state), per-node solid bytes, the per-chunk slow-path
+// bitmask, the step counters, a sticky error word and the particle arrays.
+// lbm_step replays a CUDA graph of GRAPH_STEPS timesteps; a timestep is
+//   [particle forces + Newton-Euler] -> [link exchange + re-rasterise]
+//   -> [fused pull-stream + collide over every domain]
+// where the two particle kernels are skipped when no domain holds particles.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "kernels.h"
+
+using namespace lbmk;
+
+namespace {
+
+constexpr int GRAPH_STEPS = 8;  // even, so a replay returns to the same arena
+thread_local std::string g_create_error = "no error";
+
+size_t elem_bytes(int kind) { return kind == 0 ? 8 : (kind <= 2 ? 4 : 2); }
+
+}  // namespace
+
+struct lbm_ctx {
+    int ndom = 0;
+    int kind = 2;
+    size_t esz = 4;
+    int V = 4;
+    std::vector<lbm_params> prm;
+    std::vector<DomDev> hd;
+    std::vector<std::vector<uint8_t>> hsolid;  // host copy of each domain's mask (ny*nx)
+    DomDev* dd = nullptr;
+    int64_t* d_item_off = nullptr;
+    int64_t total_items = 0;
+    void* f[2] = {nullptr, nullptr};
+    size_t arena_elems = 0;
+    uint8_t* solid = nullptr;
+    size_t node_bytes = 0;
+    uint32_t* special = nullptr;
+    size_t special_words = 0;
+    int64_t* ctr = nullptr;   // [2]
+    unsigned* err = nullptr;  // sticky
+    bool noise = false, pl = false;
+
+    // particles: max_particles slots per domain, contiguous per domain
+    int np_slots = 0;
+    int np_active = 0;
+    std::vector<PartStatic> hst;
+    std::vector<PartState> hstate;  // host shadow used while adding
+    PartState* pcur = nullptr;
+    PartState* pnext = nullptr;
+    PartStatic* pst = nullptr;
+    int32_t* links = nullptr;
+    int32_t* nlinks = nullptr;
+    int32_t* flips = nullptr;
+    int32_t* nflips = nullptr;
+    double* diag = nullptr;
+    int64_t links_total = 0, flips_total = 0;
+
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_snap = nullptr, ev_copied = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    bool graph_dirty = true;
+
+    int cur = 0;
+    int64_t steps = 0;
+    int block = 256;
+    int grid_mode = 0;  // 0: one warp item per warp; 1: persistent grid-stride
+    int64_t grid = 1;
+
+    double* d_stage = nullptr;
+    size_t d_stage_bytes = 0;
+    double* d_partial = nullptr;
+    double* d_sums = nullptr;
+    float* d_mom = nullptr;
+    float* h_mom = nullptr;
+    size_t mom_elems = 0;
+    int mom_pending = 0;
+
+    std::string msg = "no error";
+};
+
+namespace {
+
+int fail(lbm_ctx* c, int code, const std::string& m) {
+    if (c) c->msg = m;
+    else g_create_error = m;
+    return code;
+}
+
+#define CKC(ctx, call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? LBM_E_NOMEM : LBM_E_CUDA,    \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                \
+    } while (0)
+
+int validate(const lbm_params& p, int d, lbm_ctx* c) {
+    char b[256];
+    auto bad = [&](const char* what) {
+        snprintf(b, sizeof b, "domain %d: %s", d, what);
+        return fail(c, LBM_E_INVAL, b);
+    };
+    if (p.nx < 3 || p.ny < 3) return bad("nx and ny must be >= 3");
+    if ((int64_t)p.nx * p.ny > (int64_t)1 << 28) return bad("domain larger than 2^28 nodes");
+    if ((p.periodic_x != 0) == (p.inlet_outlet != 0)) return bad("exactly one of periodic_x / inlet_outlet");
+    if ((p.periodic_y != 0) == (p.walls_y != 0)) return bad("exactly one of periodic_y / walls_y");
+    if (!(p.tau > 0.5) || !std::isfinite(p.tau)) return bad("tau must be > 1/2");
+    if (!(p.rho0 > 0.0)) return bad("rho0 must be > 0");
+    if (!(p.kT >= 0.0)) return bad("kT must be >= 0");
+    if (p.store < 0 || p.store > 4) return bad("unknown store kind");
+    if ((p.store == LBM_F16S || p.store == LBM_BF16S) && !(p.store_scale > 0.0)) return bad("store_scale must be > 0");
+    if (p.inlet_outlet && (!(p.rho_in > 0.0) || !(p.rho_out > 0.0))) return bad("rho_in / rho_out must be > 0");
+    if (p.power_law) {
+        if (!(p.n_pl > 0.0) || !(p.xi_pl > 0.0)) return bad("power law needs n > 0 and xi > 0");
+        if (!(p.tau_min > 0.5) || !(p.tau_max > p.tau_min)) return bad("power law needs 1/2 < tau_min < tau_max");
+    }
+    if (p.max_particles < 0 || p.max_particles > 4096) return bad("max_particles must be in [0, 4096]");
+    if (!(p.lj_psi >= 0.0) || !(p.lj_rit >= 0.0)) return bad("lj_psi and lj_rit must be >= 0");
+    return LBM_OK;
+}
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+void fill_dom(DomDev& D, const lbm_params& p, int kind) {
+    memset(&D, 0, sizeof D);
+    D.nx = p.nx;
+    D.ny = p.ny;
+    D.flags = (p.periodic_x ? FLAG_PX : 0) | (p.periodic_y ? FLAG_PY : 0) | (p.walls_y ? FLAG_WY : 0) |
+              (p.inlet_outlet ? FLAG_IO : 0);
+    D.V = store_vector_width(kind);
+    D.pitch = (int32_t)round_up(p.nx, std::max<int64_t>(D.V, 128 / (int64_t)elem_bytes(kind)));
+    D.plane = (int64_t)D.pitch * p.ny;
+    const int nchunks = (p.nx + D.V - 1) / D.V;
+    D.seg_per_row = (nchunks + 31) / 32;
+    D.seed = p.seed;
+    D.domain_id = p.domain_id;
+    D.tau = p.tau;
+    D.inv_tau = 1.0 / p.tau;
+    D.rho0 = p.rho0;
+    D.gx = p.gx;
+    D.gy = p.gy;
+    D.rho_in = p.rho_in;
+    D.rho_out = p.rho_out;
+    const bool shifted = kind >= 2;
+    D.drho_in = shifted ? p.rho_in - p.rho0 : p.rho_in;
+    D.drho_out = shifted ? p.rho_out - p.rho0 : p.rho_out;
+    D.kT = p.kT;
+    D.n_pl = p.power_law ? p.n_pl : 1.0;
+    D.xi_pl = p.xi_pl;
+    D.tau_min = p.tau_min;
+    D.tau_max = p.tau_max;
+    D.n_is_one = p.power_law ? (p.n_pl == 1.0) : 1;
+    if (p.power_law) {
+        D.tmin_pow = std::pow(p.tau_min, 1.0 - p.n_pl);
+        D.tmax_pow = std::pow(p.tau_max, 1.0 - p.n_pl);
+    }
+    D.lj_psi = p.lj_psi;
+    D.lj_rit = p.lj_rit;
+    const bool scaled = kind == LBM_F16S || kind == LBM_BF16S;
+    D.scale = scaled ? p.store_scale : 1.0;
+    D.inv_scale = scaled ? 1.0 / p.store_scale : 1.0;
+}
+
+// Per-chunk slow-path bits: a chunk takes the per-node path when one of its
+// nodes is solid or pulls from a solid node.
+void build_special(const DomDev& D, const uint8_t* solid, std::vector<uint32_t>& words) {
+    words.assign((size_t)D.ny * D.seg_per_row, 0u);
+    const bool px = D.flags & FLAG_PX, py = D.flags & FLAG_PY;
+    for (int y = 0; y < D.ny; ++y)
+        for (int x = 0; x < D.nx; ++x) {
+            bool sp = solid[(size_t)y * D.nx + x] != 0;
+            for (int dy = -1; dy <= 1 && !sp; ++dy)
+                for (int dx = -1; dx <= 1 && !sp; ++dx) {
+                    int sx = x + dx, sy = y + dy;
+                    if (sx < 0 || sx >= D.nx) { if (!px) continue; sx = (sx + D.nx) % D.nx; }
+                    if (sy < 0 || sy >= D.ny) { if (!py) continue; sy = (sy + D.ny) % D.ny; }
+                    sp = solid[(size_t)sy * D.nx + sx] != 0;
+                }
+            if (sp) {
+                const int c = x / D.V;
+                words[(size_t)y * D.seg_per_row + c / 32] |= 1u << (c % 32);
+            }
+        }
+}
+
+void set_launch(lbm_ctx* c) {
+    const int64_t wpb = c->block / 32;
+    int64_t full = (c->total_items + wpb - 1) / wpb;
+    if (full < 1) full = 1;
+    if (c->grid_mode == 1) {
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t per_sm = std::max<int64_t>(1, 2048 / c->block);
+        c->grid = std::min<int64_t>(full, (int64_t)sms * per_sm);
+    } else {
+        c->grid = full;
+    }
+    c->graph_dirty = true;
+}
+
+PartArgs part_args(lbm_ctx* c, int cur) {
+    PartArgs a;
+    a.doms = c->dd;
+    a.arena = c->f[cur];
+    a.solid = c->solid;
+    a.cur = c->pcur;
+    a.next = c->pnext;
+    a.st = c->pst;
+    a.np = c->np_slots;
+    a.links = c->links;
+    a.nlinks = c->nlinks;
+    a.flips = c->flips;
+    a.nflips = c->nflips;
+    a.diag = c->diag;
+    a.err = c->err;
+    return a;
+}
+
+cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int block, int64_t grid) {
+    StreamArgs a;
+    a.doms = c->dd;
+    a.item_off = c->d_item_off;
+    a.ndom = c->ndom;
+    a.total_items = c->total_items;
+    a.src = c->f[cur];
+    a.dst = c->f[cur ^ 1];
+    a.solid = c->solid;
+    a.special = c->special;
+    a.ctr_in = c->ctr + cur;
+    a.ctr_out = c->ctr + (cur ^ 1);
+    a.err = c->err;
+    return launch_stream_collide(c->kind, c->noise, c->pl, a, block, grid, s);
+}
+
+cudaError_t enqueue_step(lbm_ctx* c, int cur, cudaStream_t s) {
+    if (c->np_active > 0) {
+        const PartArgs a = part_args(c, cur);
+        cudaError_t e = launch_particle_forces(c->kind, a, s);
+        if (e != cudaSuccess) return e;
+        e = launch_particle_links(c->kind, a, true, true, s);
+        if (e != cudaSuccess) return e;
+    }
+    return enqueue_stream_collide(c, cur, s, c->block, c->grid);
+}
+
+int build_graphs(lbm_ctx* c) {
+    for (int k = 0; k < 2; ++k) {
+        if (c->gexec[k]) { cudaGraphExecDestroy(c->gexec[k]); c->gexec[k] = nullptr; }
+        cudaGraph_t g = nullptr;
+        CKC(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int s = 0; s < GRAPH_STEPS && e == cudaSuccess; ++s) e = enqueue_step(c, k ^ (s & 1), c->cap_stream);
+        cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); CKC(c, e); }
+        CKC(c, e2);
+        e = cudaGraphInstantiate(&c->gexec[k], g, 0);
+        cudaGraphDestroy(g);
+        CKC(c, e);
+    }
+    c->graph_dirty = false;
+    return LBM_OK;
+}
+
+int check_err(lbm_ctx* c) {
+    unsigned h = 0;
+    CKC(c, cudaMemcpy(&h, c->err, sizeof h, cudaMemcpyDeviceToHost));
+    if (h & ERR_UNSTABLE) return fail(c, LBM_E_UNSTABLE, "non-finite or non-positive density on the lattice");
+    if (h & ERR_TIMEOUT) return fail(c, LBM_E_TIMEOUT, "a bounded device wait ran out");
+    if (h & ERR_STATE) return fail(c, LBM_E_STATE, "particle overlap or particle list capacity exceeded");
+    return LBM_OK;
+}
+
+int sync_and_check(lbm_ctx* c) {
+    CKC(c, cudaStreamSynchronize(c->stream));
+    return check_err(c);
+}
+
+int ensure_stage(lbm_ctx* c, size_t bytes) {
+    if (c->d_stage_bytes >= bytes) return LBM_OK;
+    if (c->d_stage) cudaFree(c->d_stage);
+    c->d_stage = nullptr;
+    c->d_stage_bytes = 0;
+    CKC(c, cudaMalloc(&c->d_stage, bytes));
+    c->d_stage_bytes = bytes;
+    return LBM_OK;
+}
+
+int check_dom(lbm_ctx* c, int dom) {
+    if (!c) return LBM_E_INVAL;
+    if (dom < 0 || dom >= c->ndom) return fail(c, LBM_E_INVAL, "domain index out of range");
+    return LBM_OK;
+}
+
+void free_particles(lbm_ctx* c) {
+    cudaFree(c->pcur); cudaFree(c->pnext); cudaFree(c->pst);
+    cudaFree(c->links); cudaFree(c->nlinks); cudaFree(c->flips); cudaFree(c->nflips); cudaFree(c->diag);
+    c->pcur = c->pnext = nullptr; c->pst = nullptr;
+    c->links = c->nlinks = c->flips = c->nflips = nullptr;
+    c->diag = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->msg.c_str() : g_create_error.c_str(); }
+
+int lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
+    return lbm_create_ensemble(1, p, cuda_stream, out);
+}
+
+int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_stream, lbm_ctx** out) {
+    if (!out || !per_domain || ndom < 1 || ndom > 65536) return fail(nullptr, LBM_E_INVAL, "bad arguments to lbm_create");
+    *out = nullptr;
+    for (int d = 0; d < ndom; ++d) {
+        int r = validate(per_domain[d], d, nullptr);
+        if (r) return r;
+        if (per_domain[d].store != per_domain[0].store) return fail(nullptr, LBM_E_INVAL, "store kind differs between domains");
+    }
+    lbm_ctx* c = new lbm_ctx();
+    c->ndom = ndom;
+    c->kind = per_domain[0].store;
+    c->esz = elem_bytes(c->kind);
+    c->V = store_vector_width(c->kind);
+    c->prm.assign(per_domain, per_domain + ndom);
+    c->hd.resize(ndom);
+    c->hsolid.resize(ndom);
+    std::vector<int64_t> item_off(ndom);
+    int64_t off = 0, node_off = 0, mask_off = 0, items = 0;
+    int pslot = 0;
+    for (int d = 0; d < ndom; ++d) {
+        DomDev& D = c->hd[d];
+        fill_dom(D, per_domain[d], c->kind);
+        D.off = off;
+        D.node_off = node_off;
+        D.mask_off = mask_off;
+        D.item_off = items;
+        D.p0 = pslot;
+        D.np = 0;
+        item_off[d] = items;
+        off += 9 * D.plane;
+        node_off += D.plane;
+        mask_off += (int64_t)D.ny * D.seg_per_row;
+        items += (int64_t)D.ny * D.seg_per_row;
+        pslot += per_domain[d].max_particles;
+        c->hsolid[d].assign((size_t)D.nx * D.ny, 0);
+        c->noise |= per_domain[d].kT > 0.0;
+        c->pl |= per_domain[d].power_law != 0;
+    }
+    c->arena_elems = (size_t)off;
+    c->node_bytes = (size_t)node_off;
+    c->special_words = (size_t)mask_off;
+    c->total_items = items;
+    c->np_slots = pslot;
+
+    auto cleanup = [&](int r) { lbm_destroy(c); return r; };
+    int r;
+#define CKCR(call)                                                                                       \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) {                                                                         \
+            g_create_error = std::string(#call) + ": " + cudaGetErrorString(e_);                          \
+            return cleanup(e_ == cudaErrorMemoryAllocation ? LBM_E_NOMEM : LBM_E_CUDA);                  \
+        }                                                                                                \
+    } while (0)
+    if (cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        CKCR(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    CKCR(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    CKCR(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CKCR(cudaEventCreateWithFlags(&c->ev_snap, cudaEventDisableTiming));
+    CKCR(cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming));
+    CKCR(cudaMalloc(&c->f[0], c->arena_elems * c->esz));
+    CKCR(cudaMalloc(&c->f[1], c->arena_elems * c->esz));
+    CKCR(cudaMalloc(&c->solid, c->node_bytes));
+    CKCR(cudaMalloc(&c->special, std::max<size_t>(1, c->special_words) * 4));
+    CKCR(cudaMalloc(&c->dd, sizeof(DomDev) * ndom));
+    CKCR(cudaMalloc(&c->d_item_off, sizeof(int64_t) * ndom));
+    CKCR(cudaMalloc(&c->ctr, sizeof(int64_t) * 2));
+    CKCR(cudaMalloc(&c->err, sizeof(unsigned)));
+    CKCR(cudaMalloc(&c->d_partial, sizeof(double) * 3 * CHECK_BLOCKS));
+    CKCR(cudaMalloc(&c->d_sums, sizeof(double) * 3));
+    CKCR(cudaMemsetAsync(c->solid, 0, c->node_bytes, c->stream));
+    CKCR(cudaMemsetAsync(c->special, 0, std::max<size_t>(1, c->special_words) * 4, c->stream));
+    CKCR(cudaMemsetAsync(c->f[1], 0, c->arena_elems * c->esz, c->stream));
+    CKCR(cudaMemsetAsync(c->ctr, 0, sizeof(int64_t) * 2, c->stream));
+    CKCR(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    CKCR(cudaMemcpyAsync(c->dd, c->hd.data(), sizeof(DomDev) * ndom, cudaMemcpyHostToDevice, c->stream));
+    CKCR(cudaMemcpyAsync(c->d_item_off, item_off.data(), sizeof(int64_t) * ndom, cudaMemcpyHostToDevice, c->stream));
+    // special bits of an all-fluid geometry are zero; rest state in arena 0
+    CKCR(launch_fill_rest(c->kind, c->dd, ndom, c->hd.data(), c->f[0], c->solid, c->stream));
+    if (c->np_slots > 0) {
+        c->hst.assign(c->np_slots, PartStatic{});
+        for (auto& s : c->hst) s.dom = -1;
+        c->hstate.assign(c->np_slots, PartState{});
+    }
+    CKCR(cudaStreamSynchronize(c->stream));
+#undef CKCR
+    set_launch(c);
+    r = LBM_OK;
+    *out = c;
+    return r;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& g : c->gexec)
+        if (g) cudaGraphExecDestroy(g);
+    cudaFree(c->f[0]); cudaFree(c->f[1]); cudaFree(c->solid); cudaFree(c->special);
+    cudaFree(c->dd); cudaFree(c->d_item_off); cudaFree(c->ctr); cudaFree(c->err);
+    cudaFree(c->d_partial); cudaFree(c->d_sums); cudaFree(c->d_stage); cudaFree(c->d_mom);
+    if (c->h_mom) cudaFreeHost(c->h_mom);
+    free_particles(c);
+    if (c->ev_snap) cudaEventDestroy(c->ev_snap);
+    if (c->ev_copied) cudaEventDestroy(c->ev_copied);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int lbm_set_geometry(lbm_ctx* c, int dom, const uint8_t* solid) {
+    int r = check_dom(c, dom);
+    if (r) return r;
+    if (!solid) return fail(c, LBM_E_INVAL, "solid mask is NULL");
+    if (c->np_active > 0) return fail(c, LBM_E_STATE, "set the geometry before adding particles");
+    const DomDev& D = c->hd[dom];
+    std::vector<uint8_t>& hs = c->hsolid[dom];
+    for (size_t k = 0; k < hs.size(); ++k) hs[k] = solid[k] ? 1 : 0;
+    std::vector<uint8_t> pitched((size_t)D.plane, 0);
+    for (int y = 0; y < D.ny; ++y) memcpy(&pitched[(size_t)y * D.pitch], &hs[(size_t)y * D.nx], D.nx);
+    std::vector<uint32_t> words;
+    build_special(D, hs.data(), words);
+    CKC(c, cudaStreamSynchronize(c->stream));
+    CKC(c, cudaMemcpy(c->solid + D.node_off, pitched.data(), pitched.size(), cudaMemcpyHostToDevice));
+    if (!words.empty())
+        CKC(c, cudaMemcpy(c->special + D.mask_off, words.data(), words.size() * 4, cudaMemcpyHostToDevice));
+    // solid nodes hold no populations: re-apply the current state with zeros there
+    r = ensure_stage(c, sizeof(double) * 9 * (size_t)D.nx * D.ny);
+    if (r) return r;
+    CKC(c, launch_export(c->kind, D, c->f[c->cur], c->solid, c->d_stage, c->stream));
+    CKC(c, launch_import(c->kind, D, c->d_stage, c->f[c->cur], c->solid, c->stream));
+    return sync_and_check(c);
+}
+
+int lbm_add_particles(lbm_ctx* c, int dom, int n, const lbm_particle* p) {
+    int r = check_dom(c, dom);
+    if (r) return r;
+    if (n < 0 || (n > 0 && !p)) return fail(c, LBM_E_INVAL, "bad particle array");
+    if (n == 0) return LBM_OK;
+    DomDev& D = c->hd[dom];
+    const lbm_params& P = c->prm[dom];
+    if (D.np + n > P.max_particles) return fail(c, LBM_E_INVAL, "more particles than max_particles");
+    for (int i = 0; i < n; ++i) {
+        const lbm_particle& q = p[i];
+        if (!(q.R > 0.5) || !(q.rho_p > 0.0) || !std::isfinite(q.x) || !std::isfinite(q.y))
+            return fail(c, LBM_E_INVAL, "particle needs R > 1/2, rho_p > 0 and a finite position");
+        if (q.x < 0 || q.x >= D.nx || q.y < 0 || q.y >= D.ny) return fail(c, LBM_E_INVAL, "particle centre outside the domain");
+        if ((D.flags & FLAG_PX) && 2 * q.R + 8 >= D.nx) return fail(c, LBM_E_INVAL, "particle too large for the periodic x extent");
+        if ((D.flags & FLAG_PY) && 2 * q.R + 8 >= D.ny) return fail(c, LBM_E_INVAL, "particle too large for the periodic y extent");
+    }
+    CKC(c, cudaStreamSynchronize(c->stream));
+    // refresh the host shadow of the existing particle states
+    if (c->np_active > 0)
+        CKC(c, cudaMemcpy(c->hstate.data(), c->pcur, sizeof(PartState) * c->np_slots, cudaMemcpyDeviceToHost));
+    const double pi = 3.14159265358979323846264338327950288;
+    for (int i = 0; i < n; ++i) {
+        const lbm_particle& q = p[i];
+        const int s = D.p0 + D.np + i;
+        PartStatic& st = c->hst[s];
+        st.R = q.R;
+        st.rho_p = q.rho_p;
+        st.m = q.rho_p * pi * q.R * q.R;
+        st.I = 0.5 * st.m * q.R * q.R;
+        st.dom = dom;
+        st.fixed = q.fixed ? 1 : 0;
+        const int r_up = (int)std::ceil(q.R);
+        st.link_cap = 32 * (2 * r_up + 3);
+        st.flip_cap = (2 * r_up + 6) * (2 * r_up + 6);
+        c->hstate[s] = PartState{q.x, q.y, q.U, q.V, q.Omega, q.theta};
+    }
+    D.np += n;
+    c->np_active += n;
+    // lay out the per-particle lists and (re)allocate them
+    int64_t lo = 0, fo = 0;
+    for (int s = 0; s < c->np_slots; ++s) {
+        PartStatic& st = c->hst[s];
+        if (st.dom < 0) continue;
+        st.link_off = lo;
+        st.flip_off = fo;
+        lo += st.link_cap;
+        fo += st.flip_cap;
+    }
+    free_particles(c);
+    const size_t ns = c->np_slots;
+    CKC(c, cudaMalloc(&c->pcur, sizeof(PartState) * ns));
+    CKC(c, cudaMalloc(&c->pnext, sizeof(PartState) * ns));
+    CKC(c, cudaMalloc(&c->pst, sizeof(PartStatic) * ns));
+    CKC(c, cudaMalloc(&c->links, sizeof(int32_t) * std::max<int64_t>(lo, 1)));
+    CKC(c, cudaMalloc(&c->flips, sizeof(int32_t) * std::max<int64_t>(fo, 1)));
+    CKC(c, cudaMalloc(&c->nlinks, sizeof(int32_t) * ns));
+    CKC(c, cudaMalloc(&c->nflips, sizeof(int32_t) * ns));
+    CKC(c, cudaMalloc(&c->diag, sizeof(double) * DIAG_N * ns));
+    CKC(c, cudaMemset(c->nlinks, 0, sizeof(int32_t) * ns));
+    CKC(c, cudaMemset(c->nflips, 0, sizeof(int32_t) * ns));
+    CKC(c, cudaMemset(c->diag, 0, sizeof(double) * DIAG_N * ns));
+    CKC(c, cudaMemcpy(c->pcur, c->hstate.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
+    CKC(c, cudaMemcpy(c->pnext, c->hstate.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
+    CKC(c, cudaMemcpy(c->pst, c->hst.data(), sizeof(PartStatic) * ns, cudaMemcpyHostToDevice));
+    CKC(c, cudaMemcpy(c->dd + dom, &D, sizeof(DomDev), cudaMemcpyHostToDevice));
+    c->links_total = lo;
+    c->flips_total = fo;
+    // rasterise every particle at its current position (no link exchange, no flips)
+    CKC(c, launch_particle_links(c->kind, part_args(c, c->cur), false, false, c->stream));
+    c->graph_dirty = true;
+    return sync_and_check(c);
+}
+
+int lbm_set_populations(lbm_ctx* c, int dom, const double* f) {
+    int r = check_dom(c, dom);
+    if (r) return r;
+    if (!f) return fail(c, LBM_E_INVAL, "population array is NULL");
+    const DomDev& D = c->hd[dom];
+    const size_t bytes = sizeof(double) * 9 * (size_t)D.nx * D.ny;
+    r = ensure_stage(c, bytes);
+    if (r) return r;
+    CKC(c, cudaMemcpyAsync(c->d_stage, f, bytes, cudaMemcpyHostToDevice, c->stream));
+    CKC(c, launch_import(c->kind, D, c->d_stage, c->f[c->cur], c->solid, c->stream));
+    return sync_and_check(c);
+}
+
+int lbm_get_populations(lbm_ctx* c, int dom, double* f) {
+    int r = check_dom(c, dom);
+    if (r) return r;
+    if (!f) return fail(c, LBM_E_INVAL, "population array is NULL");
+    const DomDev& D = c->hd[dom];
+    const size_t bytes = sizeof(double) * 9 * (size_t)D.nx * D.ny;
+    r = ensure_stage(c, bytes);
+    if (r) return r;
+    CKC(c, launch_export(c->kind, D, c->f[c->cur], c->solid, c->d_stage, c->stream));
+    CKC(c, cudaMemcpyAsync(f, c->d_stage, bytes, cudaMemcpyDeviceToHost, c->stream));
+    return sync_and_check(c);
+}
+
+int lbm_step(lbm_ctx* c, int64_t nsteps) {
+    if (!c) return LBM_E_INVAL;
+    if (nsteps < 0) return fail(c, LBM_E_INVAL, "nsteps must be >= 0");
+    if (nsteps == 0) return LBM_OK;
+    if (c->graph_dirty) {
+        int r = build_graphs(c);
+        if (r) return r;
+    }
+    int64_t left = nsteps;
+    while (left >= GRAPH_STEPS) {
+        CKC(c, cudaGraphLaunch(c->gexec[c->cur], c->stream));
+        left -= GRAPH_STEPS;
+    }
+    while (left > 0) {
+        CKC(c, enqueue_step(c, c->cur, c->stream));
+        c->cur ^= 1;
+        --left;
+    }
+    c->steps += nsteps;
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx* c) {
+    if (!c) return LBM_E_INVAL;
+    return sync_and_check(c);
+}
+
+int64_t lbm_step_count(const lbm_ctx* c) { return c ? c->steps : -1; }
+
+int lbm_moments(lbm_ctx* c, int dom, double* rho, double* ux, double* uy) {
+    int r = check_dom(c, dom);
+    if (r) return r;
+    if (!rho || !ux || !uy) return fail(c, LBM_E_INVAL, "moment arrays must not be NULL");
+    const DomDev& D = c->hd[dom];
+    const size_t n = (size_t)D.nx * D.ny;
+    r = ensure_stage(c, sizeof(double) * 3 * n);
+    if (r) return r;
+    CKC(c, launch_moments(c->kind, D, c->f[c->cur], c->solid, c->d_stage, c->d_stage + n, c->d_stage + 2 * n, false,
+                          c->stream));
+    CKC(c, cudaMemcpyAsync(rho, c->d_stage, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    CKC(c, cudaMemcpyAsync(ux, c->d_stage + n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    CKC(c, cudaMemcpyAsync(uy, c->d_stage + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    return sync_and_check(c);
+}
+
+int lbm_moments_device(lbm_ctx* c, int dom, float* d_rho, float* d_ux, float* d_uy) {
+    int r = check_dom(c, dom);
+    if (r) return r;
+    if (!d_rho || !d_ux || !d_uy) return fail(c, LBM_E_INVAL, "moment arrays must not be NULL");
+    CKC(c, launch_moments(c->kind, c->hd[dom], c->f[c->cur], c->solid, d_rho, d_ux, d_uy, true, c->stream));
+    return LBM_OK;
+}
+
+int lbm_moments_async(lbm_ctx* c, int dom) {
+    int r = check_dom(c, dom);
+    if (r) return r;
+    const DomDev& D = c->hd[dom];
+    const size_t n = (size_t)D.nx * D.ny;
+    if (c->mom_pending) CKC(c, cudaEventSynchronize(c->ev_copied));
+    if (c->mom_elems < 3 * n) {
+        cudaFree(c->d_mom);
+        if (c->h_mom) cudaFreeHost(c->h_mom);
+        c->d_mom = nullptr;
+        c->h_mom = nullptr;
+        c->mom_elems = 0;
+        CKC(c, cudaMalloc(&c->d_mom, sizeof(float) * 3 * n));
+        CKC(c, cudaMallocHost(&c->h_mom, sizeof(float) * 3 * n));
+        c->mom_elems = 3 * n;
+    }
+    // snapshot on the main stream (a read of the state), copy on the side stream
+    CKC(c, launch_moments(c->kind, D, c->f[c->cur], c->solid, c->d_mom, c->d_mom + n, c->d_mom + 2 * n, true,
+                          c->stream));
+    CKC(c, cudaEventRecord(c->ev_snap, c->stream));
+    CKC(c, cudaStreamWaitEvent(c->side, c->ev_snap, 0));
+    CKC(c, cudaMemcpyAsync(c->h_mom, c->d_mom, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, c->side));
+    CKC(c, cudaEventRecord(c->ev_copied, c->side));
+    c->mom_pending = (int)n;
+    return LBM_OK;
+}
+
+int lbm_moments_async_wait(lbm_ctx* c, float* rho, float* ux, float* uy) {
+    if (!c) return LBM_E_INVAL;
+    if (!c->mom_pending) return fail(c, LBM_E_STATE, "no asynchronous moment copy in flight");
+    CKC(c, cudaEventSynchronize(c->ev_copied));
+    const size_t n = (size_t)c->mom_pending;
+    if (rho) memcpy(rho, c->h_mom, sizeof(float) * n);
+    if (ux) memcpy(ux, c->h_mom + n, sizeof(float) * n);
+    if (uy) memcpy(uy, c->h_mom + 2 * n, sizeof(float) * n);
+    c->mom_pending = 0;
+    return check_err(c);
+}
+
+int lbm_particles(lbm_ctx* c, int dom, lbm_particle* out, int cap) {
+    int r = check_dom(c, dom);
+    if (r) return r;
+    const DomDev& D = c->hd[dom];
+    if (D.np == 0) return 0;
+    std::vector<PartState> s(D.np);
+    CKC(c, cudaMemcpyAsync(s.data(), c->pcur + D.p0, sizeof(PartState) * D.np, cudaMemcpyDeviceToHost, c->stream));
+    r = sync_and_check(c);
+    if (r) return r;
+    for (int i = 0; i < D.np && i < cap && out; ++i) {
+        const PartStatic& st = c->hst[D.p0 + i];
+        out[i] = lbm_particle{s[i].x, s[i].y, st.R, st.rho_p, s[i].U, s[i].V, s[i].Om, s[i].th, st.fixed, 0};
+    }
+    return D.np;
+}
+
+int lbm_particle_forces(lbm_ctx* c, int dom, int i, double* out13) {
+    int r = check_dom(c, dom);
+    if (r) return r;
+    const DomDev& D = c->hd[dom];
+    if (i < 0 || i >= D.np || !out13) return fail(c, LBM_E_INVAL, "particle index out of range");
+    CKC(c, cudaMemcpyAsync(out13, c->diag + (int64_t)(D.p0 + i) * DIAG_N, sizeof(double) * DIAG_N,
+                           cudaMemcpyDeviceToHost, c->stream));
+    return sync_and_check(c);
+}
+
+int lbm_checks(lbm_ctx* c, int dom, double* out3) {
+    int r = check_dom(c, dom);
+    if (r) return r;
+    if (!out3) return fail(c, LBM_E_INVAL, "output is NULL");
+    CKC(c, launch_checks(c->kind, c->hd[dom], c->f[c->cur], c->solid, c->d_partial, CHECK_BLOCKS, c->d_sums, c->stream));
+    CKC(c, cudaMemcpyAsync(out3, c->d_sums, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
+    return sync_and_check(c);
+}
+
+// ---- checkpoint ---------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int32_t version, kind, ndom, np_slots;
+    int64_t steps, arena_elems, links_total, flips_total;
+};
+}  // namespace
+
+int lbm_save(lbm_ctx* c, const char* path) {
+    if (!c || !path) return LBM_E_INVAL;
+    int r = sync_and_check(c);
+    if (r) return r;
+    FILE* fp = fopen(path, "wb");
+    if (!fp) return fail(c, LBM_E_IO, std::string("cannot open ") + path);
+    CkptHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, "LBMGB300", 8);
+    h.version = 1;
+    h.kind = c->kind;
+    h.ndom = c->ndom;
+    h.np_slots = c->np_slots;
+    h.steps = c->steps;
+    h.arena_elems = (int64_t)c->arena_elems;
+    h.links_total = c->links_total;
+    h.flips_total = c->flips_total;
+    bool ok = fwrite(&h, sizeof h, 1, fp) == 1;
+    ok = ok && fwrite(c->prm.data(), sizeof(lbm_params), c->ndom, fp) == (size_t)c->ndom;
+    for (int d = 0; d < c->ndom && ok; ++d) ok = fwrite(&c->hd[d].np, sizeof(int32_t), 1, fp) == 1;
+    std::vector<char> buf(c->arena_elems * c->esz);
+    int64_t ctr = 0;
+    if (ok && cudaMemcpy(buf.data(), c->f[c->cur], buf.size(), cudaMemcpyDeviceToHost) != cudaSuccess) ok = false;
+    if (ok && cudaMemcpy(&ctr, c->ctr + c->cur, sizeof ctr, cudaMemcpyDeviceToHost) != cudaSuccess) ok = false;
+    ok = ok && fwrite(&ctr, sizeof ctr, 1, fp) == 1 && fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+    for (int d = 0; d < c->ndom && ok; ++d)
+        ok = fwrite(c->hsolid[d].data(), 1, c->hsolid[d].size(), fp) == c->hsolid[d].size();
+    if (ok && c->np_slots > 0 && c->np_active > 0) {
+        const size_t ns = c->np_slots;
+        std::vector<PartState> s(ns);
+        std::vector<int32_t> nl(ns), nf(ns), L(std::max<int64_t>(c->links_total, 1)), F(std::max<int64_t>(c->flips_total, 1));
+        std::vector<double> dg(ns * DIAG_N);
+        ok = cudaMemcpy(s.data(), c->pcur, sizeof(PartState) * ns, cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(nl.data(), c->nlinks, 4 * ns, cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(nf.data(), c->nflips, 4 * ns, cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(L.data(), c->links, 4 * L.size(), cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(F.data(), c->flips, 4 * F.size(), cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(dg.data(), c->diag, 8 * dg.size(), cudaMemcpyDeviceToHost) == cudaSuccess;
+        ok = ok && fwrite(c->hst.data(), sizeof(PartStatic), ns, fp) == ns && fwrite(s.data(), sizeof(PartState), ns, fp) == ns &&
+             fwrite(nl.data(), 4, ns, fp) == ns && fwrite(nf.data(), 4, ns, fp) == ns &&
+             fwrite(L.data(), 4, L.size(), fp) == L.size() && fwrite(F.data(), 4, F.size(), fp) == F.size() &&
+             fwrite(dg.data(), 8, dg.size(), fp) == dg.size();
+    }
+    ok = (fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : fail(c, LBM_E_IO, std::string("write failed: ") + path);
+}
+
+int lbm_load(lbm_ctx* c, const char* path) {
+    if (!c || !path) return LBM_E_INVAL;
+    int r = sync_and_check(c);
+    if (r) return r;
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return fail(c, LBM_E_IO, std::string("cannot open ") + path);
+    auto bail = [&](const char* m) { fclose(fp); return fail(c, LBM_E_IO, m); };
+    CkptHeader h;
+    if (fread(&h, sizeof h, 1, fp) != 1 || memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 1) return bail("not a checkpoint");
+    if (h.kind != c->kind || h.ndom != c->ndom || h.np_slots != c->np_slots || h.arena_elems != (int64_t)c->arena_elems)
+        return bail("checkpoint does not match this context");
+    std::vector<lbm_params> prm(c->ndom);
+    if (fread(prm.data(), sizeof(lbm_params), c->ndom, fp) != (size_t)c->ndom) return bail("truncated checkpoint");
+    for (int d = 0; d < c->ndom; ++d)
+        if (prm[d].nx != c->prm[d].nx || prm[d].ny != c->prm[d].ny) return bail("checkpoint domain sizes differ");
+    std::vector<int32_t> dnp(c->ndom);
+    for (int d = 0; d < c->ndom; ++d)
+        if (fread(&dnp[d], sizeof(int32_t), 1, fp) != 1) return bail("truncated checkpoint");
+    int64_t ctr = 0;
+    std::vector<char> buf(c->arena_elems * c->esz);
+    if (fread(&ctr, sizeof ctr, 1, fp) != 1 || fread(buf.data(), 1, buf.size(), fp) != buf.size()) return bail("truncated checkpoint");
+    std::vector<std::vector<uint8_t>> sol(c->ndom);
+    for (int d = 0; d < c->ndom; ++d) {
+        sol[d].resize(c->hsolid[d].size());
+        if (fread(sol[d].data(), 1, sol[d].size(), fp) != sol[d].size()) return bail("truncated checkpoint");
+    }
+    const int np_total = [&] { int s = 0; for (int v : dnp) s += v; return s; }();
+    std::vector<PartStatic> hst;
+    std::vector<PartState> s;
+    std::vector<int32_t> nl, nf, L, F;
+    std::vector<double> dg;
+    if (np_total > 0) {
+        const size_t ns = c->np_slots;
+        hst.resize(ns); s.resize(ns); nl.resize(ns); nf.resize(ns);
+        L.resize(std::max<int64_t>(h.links_total, 1));
+        F.resize(std::max<int64_t>(h.flips_total, 1));
+        dg.resize(ns * DIAG_N);
+        bool ok = fread(hst.data(), sizeof(PartStatic), ns, fp) == ns && fread(s.data(), sizeof(PartState), ns, fp) == ns &&
+                  fread(nl.data(), 4, ns, fp) == ns && fread(nf.data(), 4, ns, fp) == ns &&
+                  fread(L.data(), 4, L.size(), fp) == L.size() && fread(F.data(), 4, F.size(), fp) == F.size() &&
+                  fread(dg.data(), 8, dg.size(), fp) == dg.size();
+        if (!ok) return bail("truncated checkpoint");
+    }
+    fclose(fp);
+    // geometry first (it rewrites solid nodes of the current arena), then the state
+    for (int d = 0; d < c->ndom; ++d) {
+        c->hd[d].np = 0;
+        c->np_active = 0;
+        r = lbm_set_geometry(c, d, sol[d].data());
+        if (r) return r;
+    }
+    CKC(c, cudaMemcpy(c->f[c->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice));
+    CKC(c, cudaMemcpy(c->ctr + c->cur, &ctr, sizeof ctr, cudaMemcpyHostToDevice));
+    if (np_total > 0) {
+        const size_t ns = c->np_slots;
+        free_particles(c);
+        c->hst = hst;
+        c->hstate = s;
+        CKC(c, cudaMalloc(&c->pcur, sizeof(PartState) * ns));
+        CKC(c, cudaMalloc(&c->pnext, sizeof(PartState) * ns));
+        CKC(c, cudaMalloc(&c->pst, sizeof(PartStatic) * ns));
+        CKC(c, cudaMalloc(&c->links, 4 * L.size()));
+        CKC(c, cudaMalloc(&c->flips, 4 * F.size()));
+        CKC(c, cudaMalloc(&c->nlinks, 4 * ns));
+        CKC(c, cudaMalloc(&c->nflips, 4 * ns));
+        CKC(c, cudaMalloc(&c->diag, 8 * ns * DIAG_N));
+        CKC(c, cudaMemcpy(c->pcur, s.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
+        CKC(c, cudaMemcpy(c->pnext, s.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
+        CKC(c, cudaMemcpy(c->pst, hst.data(), sizeof(PartStatic) * ns, cudaMemcpyHostToDevice));
+        CKC(c, cudaMemcpy(c->nlinks, nl.data(), 4 * ns, cudaMemcpyHostToDevice));
+        CKC(c, cudaMemcpy(c->nflips, nf.data(), 4 * ns, cudaMemcpyHostToDevice));
+        CKC(c, cudaMemcpy(c->links, L.data(), 4 * L.size(), cudaMemcpyHostToDevice));
+        CKC(c, cudaMemcpy(c->flips, F.data(), 4 * F.size(), cudaMemcpyHostToDevice));
+        CKC(c, cudaMemcpy(c->diag, dg.data(), 8 * dg.size(), cudaMemcpyHostToDevice));
+        c->links_total = h.links_total;
+        c->flips_total = h.flips_total;
+        for (int d = 0; d < c->ndom; ++d) c->hd[d].np = dnp[d];
+        c->np_active = np_total;
+        CKC(c, cudaMemcpy(c->dd, c->hd.data(), sizeof(DomDev) * c->ndom, cudaMemcpyHostToDevice));
+    }
+    c->steps = h.steps;
+    c->graph_dirty = true;
+    return LBM_OK;
+}
+
+int lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double* ms_out3, int64_t* launches_out) {
+    if (!c || !ms_out3 || nsteps < 0) return c ? fail(c, LBM_E_INVAL, "bad arguments") : LBM_E_INVAL;
+    int r = sync_and_check(c);
+    if (r) return r;
+    const int NE = 6;
+    cudaEvent_t ev[NE];
+    for (int k = 0; k < NE; ++k) CKC(c, cudaEventCreate(&ev[k]));
+    double acc[3] = {0.0, 0.0, 0.0};
+    int64_t launches = 0;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        const bool parts = c->np_active > 0;
+        if (parts) {
+            const PartArgs a = part_args(c, c->cur);
+            CKC(c, cudaEventRecord(ev[0], c->stream));
+            CKC(c, launch_particle_forces(c->kind, a, c->stream));
+            CKC(c, cudaEventRecord(ev[1], c->stream));
+            CKC(c, launch_particle_links(c->kind, a, true, true, c->stream));
+            CKC(c, cudaEventRecord(ev[2], c->stream));
+            launches += 2;
+        }
+        CKC(c, cudaEventRecord(ev[3], c->stream));
+        CKC(c, enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid));
+        CKC(c, cudaEventRecord(ev[4], c->stream));
+        launches += 1;
+        CKC(c, cudaEventSynchronize(ev[4]));
+        float ms = 0.f;
+        if (parts) {
+            CKC(c, cudaEventElapsedTime(&ms, ev[0], ev[1]));
+            acc[0] += ms;
+            CKC(c, cudaEventElapsedTime(&ms, ev[1], ev[2]));
+            acc[1] += ms;
+        }
+        CKC(c, cudaEventElapsedTime(&ms, ev[3], ev[4]));
+        acc[2] += ms;
+        c->cur ^= 1;
+        c->steps += 1;
+    }
+    for (int k = 0; k < NE; ++k) cudaEventDestroy(ev[k]);
+    for (int k = 0; k < 3; ++k) ms_out3[k] = acc[k];
+    if (launches_out) *launches_out = launches;
+    return check_err(c);
+}
+
+int lbm_autotune(lbm_ctx* c, int trial_steps) {
+    if (!c) return LBM_E_INVAL;
+    if (trial_steps < 1) trial_steps = 20;
+    int r = sync_and_check(c);
+    if (r) return r;
+    // Trials write only the scratch arena f[cur^1] and its step counter, both
+    // of which the next real step overwrites; the state f[cur] is read-only.
+    const int blocks[] = {128, 256, 512};
+    cudaEvent_t e0, e1;
+    CKC(c, cudaEventCreate(&e0));
+    CKC(c, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_block = c->block, best_mode = c->grid_mode;
+    const int save_block = c->block, save_mode = c->grid_mode;
+    for (int mode = 0; mode < 2; ++mode)
+        for (int b : blocks) {
+            c->block = b;
+            c->grid_mode = mode;
+            set_launch(c);
+            cudaError_t e = enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid);
+            if (e != cudaSuccess) continue;
+            cudaEventRecord(e0, c->stream);
+            for (int s = 0; s < trial_steps && e == cudaSuccess; ++s)
+                e = enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid);
+            cudaEventRecord(e1, c->stream);
+            if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) continue;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_block = b; best_mode = mode; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->block = best_block;
+    c->grid_mode = best_mode;
+    set_launch(c);
+    (void)save_block;
+    (void)save_mode;
+    return sync_and_check(c);
+}
+
+}  // extern "C"

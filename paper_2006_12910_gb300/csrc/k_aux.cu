@@ -1,0 +1,189 @@
+// k_aux.cu -- state set-up, conversion, moment output and global checks of
+// the GB300 D2Q9 library.  Off the per-step hot path except when a caller
+// asks for moments or checks.
+#include "kernels.h"
+#include "lbm_dev.cuh"
+
+namespace lbmk {
+
+// Stored element of plane i -> full population value in FP64.
+template <class S>
+__device__ __forceinline__ double load_full(const typename S::T* p, const DomDev& D, int i) {
+    const double v = (double)to_a(*p, (typename S::A)D.inv_scale);
+    return S::SHIFT ? v + wgt(i) * D.rho0 : v;
+}
+template <class S>
+__device__ __forceinline__ void store_full(typename S::T* p, const DomDev& D, int i, double f) {
+    const double v = S::SHIFT ? f - wgt(i) * D.rho0 : f;
+    from_a((typename S::A)v, (typename S::A)D.scale, *p);
+}
+
+template <class S>
+__global__ void k_fill_rest(DomDev D, typename S::T* arena, const uint8_t* solid) {
+    const int64_t n = (int64_t)D.ny * D.pitch;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(k % D.pitch);
+        const bool fluid = x < D.nx && !solid[D.node_off + k];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            typename S::T* p = arena + D.off + (int64_t)i * D.plane + k;
+            if (fluid) store_full<S>(p, D, i, wgt(i) * D.rho0);
+            else from_a((typename S::A)0, (typename S::A)1, *p);
+        }
+    }
+}
+
+template <class S>
+__global__ void k_import(DomDev D, const double* in, typename S::T* arena, const uint8_t* solid) {
+    const int64_t n = (int64_t)D.nx * D.ny;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(k / D.nx), x = (int)(k - (int64_t)y * D.nx);
+        const int64_t ni = (int64_t)y * D.pitch + x;
+        const bool fluid = !solid[D.node_off + ni];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            typename S::T* p = arena + D.off + (int64_t)i * D.plane + ni;
+            if (fluid) store_full<S>(p, D, i, in[(int64_t)i * n + k]);
+            else from_a((typename S::A)0, (typename S::A)1, *p);
+        }
+    }
+}
+
+template <class S>
+__global__ void k_export(DomDev D, const typename S::T* arena, const uint8_t* solid, double* out) {
+    const int64_t n = (int64_t)D.nx * D.ny;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(k / D.nx), x = (int)(k - (int64_t)y * D.nx);
+        const int64_t ni = (int64_t)y * D.pitch + x;
+        const bool fluid = !solid[D.node_off + ni];
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            out[(int64_t)i * n + k] = fluid ? load_full<S>(arena + D.off + (int64_t)i * D.plane + ni, D, i) : 0.0;
+    }
+}
+
+template <class S, typename O>
+__global__ void k_moments(DomDev D, const typename S::T* arena, const uint8_t* solid, O* rho_o, O* ux_o, O* uy_o) {
+    const int64_t n = (int64_t)D.nx * D.ny;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(k / D.nx), x = (int)(k - (int64_t)y * D.nx);
+        const int64_t ni = (int64_t)y * D.pitch + x;
+        if (solid[D.node_off + ni]) { rho_o[k] = 0; ux_o[k] = 0; uy_o[k] = 0; continue; }
+        double r = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double fi = load_full<S>(arena + D.off + (int64_t)i * D.plane + ni, D, i);
+            r += fi;
+            jx += fi * cx(i);
+            jy += fi * cy(i);
+        }
+        rho_o[k] = (O)r;
+        ux_o[k] = (O)((jx - 0.5 * r * D.gx) / r);
+        uy_o[k] = (O)((jy - 0.5 * r * D.gy) / r);
+    }
+}
+
+// Stage 1: every block sums its grid-stride share in a fixed order, then a
+// fixed shared-memory tree; stage 2 adds the block partials in block order.
+template <class S>
+__global__ void __launch_bounds__(256) k_checks_partial(DomDev D, const typename S::T* arena, const uint8_t* solid,
+                                                        double* partial) {
+    __shared__ double sh[3][256];
+    const int64_t n = (int64_t)D.nx * D.ny;
+    double m = 0.0, px = 0.0, py = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(k / D.nx), x = (int)(k - (int64_t)y * D.nx);
+        const int64_t ni = (int64_t)y * D.pitch + x;
+        if (solid[D.node_off + ni]) continue;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double fi = load_full<S>(arena + D.off + (int64_t)i * D.plane + ni, D, i);
+            m += fi;
+            px += fi * cx(i);
+            py += fi * cy(i);
+        }
+    }
+    sh[0][threadIdx.x] = m;
+    sh[1][threadIdx.x] = px;
+    sh[2][threadIdx.x] = py;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) partial[blockIdx.x * 3 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_checks_final(const double* partial, int nblocks, double* out) {
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += partial[b * 3 + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+static int64_t blocks_for(int64_t n, int block) {
+    int64_t b = (n + block - 1) / block;
+    return b < 1 ? 1 : (b > 65535 * 16 ? 65535 * 16 : b);
+}
+
+#define LBM_DISPATCH(kind, CALL)                      \
+    switch (kind) {                                   \
+        case 0: { typedef StF64 S; CALL; } break;     \
+        case 1: { typedef StF32 S; CALL; } break;     \
+        case 2: { typedef StF32S S; CALL; } break;    \
+        case 3: { typedef StF16S S; CALL; } break;    \
+        case 4: { typedef StBF16S S; CALL; } break;   \
+        default: return cudaErrorInvalidValue;        \
+    }
+
+cudaError_t launch_fill_rest(int kind, const DomDev*, int ndom, const DomDev* hdoms, void* arena,
+                             const uint8_t* solid, cudaStream_t s) {
+    for (int d = 0; d < ndom; ++d) {
+        const DomDev& D = hdoms[d];
+        const int64_t nb = blocks_for((int64_t)D.ny * D.pitch, 256);
+        LBM_DISPATCH(kind, (k_fill_rest<S><<<(unsigned)nb, 256, 0, s>>>(D, static_cast<S::T*>(arena), solid)));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_import(int kind, const DomDev& D, const double* in, void* arena, const uint8_t* solid,
+                          cudaStream_t s) {
+    const int64_t nb = blocks_for((int64_t)D.nx * D.ny, 256);
+    LBM_DISPATCH(kind, (k_import<S><<<(unsigned)nb, 256, 0, s>>>(D, in, static_cast<S::T*>(arena), solid)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(int kind, const DomDev& D, const void* arena, const uint8_t* solid, double* out,
+                          cudaStream_t s) {
+    const int64_t nb = blocks_for((int64_t)D.nx * D.ny, 256);
+    LBM_DISPATCH(kind, (k_export<S><<<(unsigned)nb, 256, 0, s>>>(D, static_cast<const S::T*>(arena), solid, out)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int kind, const DomDev& D, const void* arena, const uint8_t* solid, void* rho,
+                           void* ux, void* uy, bool out_f32, cudaStream_t s) {
+    const int64_t nb = blocks_for((int64_t)D.nx * D.ny, 256);
+    if (out_f32) {
+        LBM_DISPATCH(kind, (k_moments<S, float><<<(unsigned)nb, 256, 0, s>>>(
+                                D, static_cast<const S::T*>(arena), solid, (float*)rho, (float*)ux, (float*)uy)));
+    } else {
+        LBM_DISPATCH(kind, (k_moments<S, double><<<(unsigned)nb, 256, 0, s>>>(
+                                D, static_cast<const S::T*>(arena), solid, (double*)rho, (double*)ux, (double*)uy)));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_checks(int kind, const DomDev& D, const void* arena, const uint8_t* solid, double* partial,
+                          int nblocks, double* out, cudaStream_t s) {
+    LBM_DISPATCH(kind, (k_checks_partial<S><<<nblocks, 256, 0, s>>>(D, static_cast<const S::T*>(arena), solid, partial)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_checks_final<<<1, 32, 0, s>>>(partial, nblocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmk

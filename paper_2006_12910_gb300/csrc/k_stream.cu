@@ -1,0 +1,181 @@
+// k_stream.cu -- fused pull-stream + collide kernel of the D2Q9 hot path
+// (arXiv:2006.12910 Sec. 2 Eq. e.LB1 with the collision of Eq. e.LB2, the
+// noise of Sec. 4 and the local tau* of Sec. 5; halfway bounce-back of Sec. 3).
+//
+// Layout: structure of arrays, plane i of domain d at arena[off + i*plane],
+// rows of `pitch` elements, x fastest.  The stored values are the
+// post-collision populations f*(t).  Each lane owns V consecutive nodes of
+// one row (V*sizeof(T) = 16 bytes), a warp owns 32 such chunks; a work item
+// is one (domain, row, warp segment).  For every direction the lane loads the
+// 16-byte vector of the source row and, for the two x-shifted families, one
+// extra element at the chunk edge (served by L1 from the neighbour lane's
+// sector), then collides in registers and writes 16-byte vectors.
+//
+// Chunks touching an x edge, a wall row, a solid node or a solid neighbour
+// (flagged in a per-row bitmask written once from the geometry) take a
+// per-node path with explicit boundary logic and scalar accesses.
+#include "kernels.h"
+#include "lbm_dev.cuh"
+
+namespace lbmk {
+
+__device__ __forceinline__ int find_domain(const int64_t* __restrict__ item_off, int ndom, int64_t g) {
+    int lo = 0, hi = ndom - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(item_off + mid) <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per-node path: pull with halfway bounce-back at walls / solids, wall-corner
+// reflection and Zou-He on the open columns, then collide and store scalars.
+template <class S, bool NOISE, bool PL>
+__device__ __forceinline__ bool slow_node(const DomDev& D, int x, int y, const typename S::T* __restrict__ base,
+                                          typename S::T* __restrict__ obase, const uint8_t* __restrict__ solid,
+                                          uint32_t step) {
+    typedef typename S::A A;
+    const int nx = D.nx, ny = D.ny, pitch = D.pitch, flags = D.flags;
+    const int64_t ni = (int64_t)y * pitch + x;
+    if (__ldg(solid + D.node_off + ni)) return true;  // solid nodes hold no populations
+    const A inv = (A)D.inv_scale;
+    const bool corner_row = (flags & FLAG_WY) && (y == 0 || y == ny - 1);
+    A f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        int sx = x - cx(i), sy = y - cy(i);
+        bool bb = false, unknown = false;
+        if (sy < 0 || sy >= ny) {
+            if (flags & FLAG_WY) bb = true;
+            else sy = sy < 0 ? sy + ny : sy - ny;
+        }
+        if (!bb && (sx < 0 || sx >= nx)) {
+            if (flags & FLAG_PX) sx = sx < 0 ? sx + nx : sx - nx;
+            else if (corner_row) bb = true;
+            else unknown = true;
+        }
+        if (!bb && !unknown && __ldg(solid + D.node_off + (int64_t)sy * pitch + sx)) bb = true;
+        if (bb) f[i] = load_one<S>(base + (int64_t)opp(i) * D.plane + ni, inv);
+        else if (unknown) f[i] = (A)0;
+        else f[i] = load_one<S>(base + (int64_t)i * D.plane + (int64_t)sy * pitch + sx, inv);
+    }
+    if ((flags & FLAG_IO) && !corner_row && (x == 0 || x == nx - 1)) {
+        if (x == 0) zou_he<A>(f, 0, (A)D.rho_in, S::SHIFT ? (A)D.drho_in : (A)D.rho_in);
+        else zou_he<A>(f, 1, (A)D.rho_out, S::SHIFT ? (A)D.drho_out : (A)D.rho_out);
+    }
+    const bool ok = collide_node<A, S::SHIFT, NOISE, PL>(f, D, (uint32_t)((int64_t)y * nx + x), step);
+    const A scl = (A)D.scale;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) from_a(f[i], scl, obase[(int64_t)i * D.plane + ni]);
+    return ok;
+}
+
+template <class S, bool NOISE, bool PL>
+__global__ void __launch_bounds__(512) k_stream_collide(StreamArgs a) {
+    typedef typename S::T T;
+    typedef typename S::A A;
+    constexpr int V = S::V;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t step64 = *a.ctr_in;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.ctr_out = step64 + 1;
+    const uint32_t step = (uint32_t)step64;
+    const T* __restrict__ src = static_cast<const T*>(a.src);
+    T* __restrict__ dst = static_cast<T*>(a.dst);
+    bool ok = true;
+
+    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < a.total_items; g += nwarps) {
+        const int d = a.ndom == 1 ? 0 : find_domain(a.item_off, a.ndom, g);
+        const DomDev& D = a.doms[d];
+        const int local = (int)(g - D.item_off);
+        const int y = local / D.seg_per_row;
+        const int seg = local - y * D.seg_per_row;
+        const int x0 = (seg * 32 + lane) * V;
+        const uint32_t word = __ldg(a.special + D.mask_off + (int64_t)y * D.seg_per_row + seg);
+        const int nx = D.nx, ny = D.ny;
+        if (x0 >= nx) continue;
+        const T* base = src + D.off;
+        T* obase = dst + D.off;
+        const bool special = (word >> lane) & 1u;
+        const bool edge_x = (x0 == 0) || (x0 + V >= nx);
+        const bool edge_y = (D.flags & FLAG_WY) && (y == 0 || y == ny - 1);
+        if (special || edge_x || edge_y) {
+#pragma unroll 1
+            for (int k = 0; k < V; ++k)
+                if (x0 + k < nx) ok &= slow_node<S, NOISE, PL>(D, x0 + k, y, base, obase, a.solid, step);
+            continue;
+        }
+        // Fast path: interior chunk, no solid anywhere near, rows in range or periodic.
+        const A inv = (A)D.inv_scale;
+        const int ym = y == 0 ? ny - 1 : y - 1;
+        const int yp = y == ny - 1 ? 0 : y + 1;
+        const int64_t pitch = D.pitch, plane = D.plane;
+        A f[9][V];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int row = cy(i) == 1 ? ym : (cy(i) == -1 ? yp : y);
+            const T* p = base + (int64_t)i * plane + row * pitch + x0;
+            A v[V];
+            load_vec<S>(p, v, inv);
+            if (cx(i) == 0) {
+#pragma unroll
+                for (int k = 0; k < V; ++k) f[i][k] = v[k];
+            } else if (cx(i) == 1) {  // source x-1
+                f[i][0] = load_one<S>(p - 1, inv);
+#pragma unroll
+                for (int k = 1; k < V; ++k) f[i][k] = v[k - 1];
+            } else {  // source x+1
+#pragma unroll
+                for (int k = 0; k < V - 1; ++k) f[i][k] = v[k + 1];
+                f[i][V - 1] = load_one<S>(p + V, inv);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            A n9[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) n9[i] = f[i][k];
+            ok &= collide_node<A, S::SHIFT, NOISE, PL>(n9, D, (uint32_t)(y * nx + x0 + k), step);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i][k] = n9[i];
+        }
+        const A scl = (A)D.scale;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) store_vec<S>(obase + (int64_t)i * plane + y * pitch + x0, f[i], scl);
+    }
+    if (!ok) atomicOr(a.err, ERR_UNSTABLE);
+}
+
+template <class S>
+static cudaError_t launch_kind(bool noise, bool pl, const StreamArgs& a, int block, int64_t grid, cudaStream_t s) {
+    if (noise && pl) k_stream_collide<S, true, true><<<(unsigned)grid, block, 0, s>>>(a);
+    else if (noise) k_stream_collide<S, true, false><<<(unsigned)grid, block, 0, s>>>(a);
+    else if (pl) k_stream_collide<S, false, true><<<(unsigned)grid, block, 0, s>>>(a);
+    else k_stream_collide<S, false, false><<<(unsigned)grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_collide(int kind, bool noise, bool pl, const StreamArgs& a, int block, int64_t grid,
+                                  cudaStream_t s) {
+    switch (kind) {
+        case 0: return launch_kind<StF64>(noise, pl, a, block, grid, s);
+        case 1: return launch_kind<StF32>(noise, pl, a, block, grid, s);
+        case 2: return launch_kind<StF32S>(noise, pl, a, block, grid, s);
+        case 3: return launch_kind<StF16S>(noise, pl, a, block, grid, s);
+        case 4: return launch_kind<StBF16S>(noise, pl, a, block, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int store_vector_width(int kind) {
+    switch (kind) {
+        case 0: return StF64::V;
+        case 1: return StF32::V;
+        case 2: return StF32S::V;
+        case 3: return StF16S::V;
+        case 4: return StBF16S::V;
+        default: return 0;
+    }
+}
+
+}  // namespace lbmk

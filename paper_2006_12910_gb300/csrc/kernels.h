@@ -1,0 +1,66 @@
+// kernels.h -- launch interface between the host runtime (capi.cu) and the
+// kernel translation units of the GB300 D2Q9 library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_types.h"
+
+namespace lbmk {
+
+struct StreamArgs {
+    const DomDev* doms;
+    const int64_t* item_off;  // first work item of each domain (ndom entries)
+    int ndom;
+    int64_t total_items;      // sum over domains of ny * seg_per_row
+    const void* src;          // population arena holding f*(t) (after link swaps)
+    void* dst;                // population arena receiving f*(t+1)
+    const uint8_t* solid;     // per-node solid bytes
+    const uint32_t* special;  // per-chunk slow-path bits
+    const int64_t* ctr_in;    // step counter of the source state
+    int64_t* ctr_out;         // step counter of the destination state
+    unsigned* err;            // sticky device error bits
+};
+
+cudaError_t launch_stream_collide(int kind, bool noise, bool pl, const StreamArgs& a, int block, int64_t grid,
+                                  cudaStream_t s);
+int store_vector_width(int kind);
+
+// ---- auxiliary kernels (k_aux.cu) ----
+// Rest state f* = omega_i rho0 on every fluid node of every domain.
+cudaError_t launch_fill_rest(int kind, const DomDev* doms, int ndom, const DomDev* hdoms, void* arena,
+                             const uint8_t* solid, cudaStream_t s);
+// Host-order FP64 f[9][ny][nx] (device buffer) -> stored populations of one domain.
+cudaError_t launch_import(int kind, const DomDev& D, const double* in, void* arena, const uint8_t* solid,
+                          cudaStream_t s);
+// Stored populations of one domain -> FP64 f[9][ny][nx] (device buffer).
+cudaError_t launch_export(int kind, const DomDev& D, const void* arena, const uint8_t* solid, double* out,
+                          cudaStream_t s);
+// rho and u = (sum f e - rho g / 2)/rho of one domain into three [ny][nx] arrays (FP64 or FP32).
+cudaError_t launch_moments(int kind, const DomDev& D, const void* arena, const uint8_t* solid, void* rho,
+                           void* ux, void* uy, bool out_f32, cudaStream_t s);
+// FP64 mass and momentum sums of one domain, deterministic two-stage reduction into out[3].
+cudaError_t launch_checks(int kind, const DomDev& D, const void* arena, const uint8_t* solid, double* partial,
+                          int nblocks, double* out, cudaStream_t s);
+constexpr int CHECK_BLOCKS = 304;
+
+// ---- particle kernels (k_part.cu) ----
+struct PartArgs {
+    const DomDev* doms;
+    void* arena;               // populations holding f*(t) (read by forces, swapped by links)
+    const uint8_t* solid;
+    PartState* cur;            // state at t (updated to t+1 by the commit phase)
+    PartState* next;           // state at t+1 written by the force phase
+    const PartStatic* st;
+    int np;
+    int32_t* links;            // per particle: (node << 3) | (k - 1), node = y*pitch + x of r_v
+    int32_t* nlinks;
+    int32_t* flips;            // per particle: (node << 1) | covered
+    int32_t* nflips;
+    double* diag;              // np * DIAG_N
+    unsigned* err;
+};
+cudaError_t launch_particle_forces(int kind, const PartArgs& a, cudaStream_t s);
+cudaError_t launch_particle_links(int kind, const PartArgs& a, bool swap, bool advance, cudaStream_t s);
+
+}  // namespace lbmk

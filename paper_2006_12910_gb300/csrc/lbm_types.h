@@ -1,0 +1,54 @@
+// lbm_types.h -- plain descriptors shared by the host runtime and the kernels
+// of the GB300 D2Q9 library (no CUDA types, no method arithmetic).
+#pragma once
+#include <stdint.h>
+
+namespace lbmk {
+
+enum : int32_t {
+    FLAG_PX = 1,   // periodic in x
+    FLAG_PY = 2,   // periodic in y
+    FLAG_WY = 4,   // halfway walls at y = -1/2 and y = ny - 1/2
+    FLAG_IO = 8,   // Zou-He density columns at x = 0 and x = nx - 1
+};
+
+enum : uint32_t {
+    ERR_UNSTABLE = 1u,  // rho <= 0 or not finite
+    ERR_STATE = 2u,     // particle overlap or list capacity exceeded
+    ERR_TIMEOUT = 4u,   // a bounded device wait ran out
+};
+
+// One lattice domain as the kernels see it.  Populations of plane i live at
+// arena[off + i*plane + y*pitch + x]; per-node bytes at nodes[node_off + y*pitch + x];
+// the special-chunk bitmask word of warp segment s of row y at
+// special[mask_off + y*seg_per_row + s] (bit = lane; a chunk is V nodes).
+struct DomDev {
+    int32_t nx, ny, pitch, flags;
+    int64_t off, plane, node_off, mask_off, item_off;
+    int32_t seg_per_row, V;
+    int32_t p0, np;           // first particle and particle count of this domain
+    int32_t n_is_one, pad0;
+    uint64_t seed;
+    uint32_t domain_id, pad1;
+    double tau, inv_tau, rho0, gx, gy;
+    double rho_in, rho_out, drho_in, drho_out;  // open-column densities (and minus rho0)
+    double kT;
+    double n_pl, xi_pl, tau_min, tau_max, tmin_pow, tmax_pow;  // tmin^(1-n), tmax^(1-n)
+    double lj_psi, lj_rit;
+    double scale, inv_scale;  // store scale of the shifted FP16/BF16 kinds (1 otherwise)
+};
+
+// Particle data on the device (Sec. 3).  State is double precision.
+struct PartState {
+    double x, y, U, V, Om, th;
+};
+struct PartStatic {
+    double R, rho_p, m, I;
+    int32_t dom, fixed;
+    int32_t link_cap, flip_cap;
+    int64_t link_off, flip_off;
+};
+
+constexpr int DIAG_N = 13;  // F_links(2), T_links, F_cu(2), T_cu, F_lj(2), T_lj, n_cov, n_unc, m_cov, m_unc
+
+}  // namespace lbmk

@@ -18,3 +18,17 @@ def oracle():
     from oracle import oracle as o
     o.build()
     return o
+
+
+@pytest.fixture
+def errlog(request):
+    """Append measured parity errors as JSON lines to $LBM_ERRLOG (if set)."""
+    import json
+
+    path = os.environ.get("LBM_ERRLOG")
+
+    def log(**kw):
+        if path:
+            with open(path, "a") as fh:
+                fh.write(json.dumps(dict(test=request.node.name, **kw), default=float) + "\n")
+    return log
