@@ -44,6 +44,7 @@ struct lbm_ctx {
     void* f[2] = {nullptr, nullptr};
     size_t arena_elems = 0;
     uint8_t* solid = nullptr;
+    uint16_t* nflags = nullptr;
     size_t node_bytes = 0;
     uint32_t* special = nullptr;
     size_t special_words = 0;
@@ -173,29 +174,60 @@ void fill_dom(DomDev& D, const lbm_params& p, int kind) {
     const bool scaled = kind == LBM_F16S || kind == LBM_BF16S;
     D.scale = scaled ? p.store_scale : 1.0;
     D.inv_scale = scaled ? 1.0 / p.store_scale : 1.0;
+    D.tau_f = (float)D.tau; D.inv_tau_f = (float)D.inv_tau; D.rho0_f = (float)D.rho0;
+    D.gx_f = (float)D.gx; D.gy_f = (float)D.gy; D.rho_in_f = (float)D.rho_in; D.rho_out_f = (float)D.rho_out;
+    D.drho_in_f = (float)D.drho_in; D.drho_out_f = (float)D.drho_out; D.kT_f = (float)D.kT;
+    D.n_pl_f = (float)D.n_pl; D.xi_pl_f = (float)D.xi_pl; D.tau_min_f = (float)D.tau_min;
+    D.tau_max_f = (float)D.tau_max; D.tmin_pow_f = (float)D.tmin_pow; D.tmax_pow_f = (float)D.tmax_pow;
+    D.scale_f = (float)D.scale; D.inv_scale_f = (float)D.inv_scale;
 }
 
-// Per-chunk slow-path bits: a chunk takes the per-node path when one of its
-// nodes is solid or pulls from a solid node.
-void build_special(const DomDev& D, const uint8_t* solid, std::vector<uint32_t>& words) {
+// Per-node flag words and per-chunk bits.  Flag bit i (1..8) marks a pulled
+// direction that bounces back: its source lies beyond a y wall, is a solid
+// node, or lies outside the x range at a wall-corner node of open ends.  Open
+// columns carry the Zou-He bits; solid nodes NF_SOLID.  A chunk bit is set
+// when any of its nodes has a nonzero flag word.
+void build_flags(const DomDev& D, const uint8_t* solid, std::vector<uint16_t>& fl, std::vector<uint32_t>& words) {
+    fl.assign((size_t)D.plane, 0);
     words.assign((size_t)D.ny * D.seg_per_row, 0u);
-    const bool px = D.flags & FLAG_PX, py = D.flags & FLAG_PY;
+    const bool px = D.flags & FLAG_PX, py = D.flags & FLAG_PY, wy = D.flags & FLAG_WY, io = D.flags & FLAG_IO;
+    static const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    static const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     for (int y = 0; y < D.ny; ++y)
         for (int x = 0; x < D.nx; ++x) {
-            bool sp = solid[(size_t)y * D.nx + x] != 0;
-            for (int dy = -1; dy <= 1 && !sp; ++dy)
-                for (int dx = -1; dx <= 1 && !sp; ++dx) {
-                    int sx = x + dx, sy = y + dy;
-                    if (sx < 0 || sx >= D.nx) { if (!px) continue; sx = (sx + D.nx) % D.nx; }
-                    if (sy < 0 || sy >= D.ny) { if (!py) continue; sy = (sy + D.ny) % D.ny; }
-                    sp = solid[(size_t)sy * D.nx + sx] != 0;
+            uint16_t f = 0;
+            const bool corner_row = wy && (y == 0 || y == D.ny - 1);
+            if (solid[(size_t)y * D.nx + x]) {
+                f = NF_SOLID;
+            } else {
+                for (int i = 1; i < 9; ++i) {
+                    int sx = x - ex[i], sy = y - ey[i];
+                    bool bb = false, unknown = false;
+                    if (sy < 0 || sy >= D.ny) {
+                        if (wy) bb = true;
+                        else sy = (sy + D.ny) % D.ny;
+                    }
+                    if (!bb && (sx < 0 || sx >= D.nx)) {
+                        if (px) sx = (sx + D.nx) % D.nx;
+                        else if (corner_row) bb = true;
+                        else unknown = true;
+                    }
+                    if (!bb && !unknown && solid[(size_t)sy * D.nx + sx]) bb = true;
+                    if (bb) f |= (uint16_t)(1u << i);
                 }
-            if (sp) {
+                if (io && !corner_row && x == 0) f |= NF_ZH_IN;
+                if (io && !corner_row && x == D.nx - 1) f |= NF_ZH_OUT;
+            }
+            (void)py;
+            fl[(size_t)y * D.pitch + x] = f;
+            if (f) {
                 const int c = x / D.V;
                 words[(size_t)y * D.seg_per_row + c / 32] |= 1u << (c % 32);
             }
         }
 }
+
+int upload_geometry(lbm_ctx* c, int dom);
 
 void set_launch(lbm_ctx* c) {
     const int64_t wpb = c->block / 32;
@@ -240,6 +272,7 @@ cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int bloc
     a.src = c->f[cur];
     a.dst = c->f[cur ^ 1];
     a.solid = c->solid;
+    a.nflags = c->nflags;
     a.special = c->special;
     a.ctr_in = c->ctr + cur;
     a.ctr_out = c->ctr + (cur ^ 1);
@@ -297,6 +330,22 @@ int ensure_stage(lbm_ctx* c, size_t bytes) {
     c->d_stage_bytes = 0;
     CKC(c, cudaMalloc(&c->d_stage, bytes));
     c->d_stage_bytes = bytes;
+    return LBM_OK;
+}
+
+// Solid bytes, flag words and chunk bits of one domain from its host mask.
+int upload_geometry(lbm_ctx* c, int dom) {
+    const DomDev& D = c->hd[dom];
+    const std::vector<uint8_t>& hs = c->hsolid[dom];
+    std::vector<uint8_t> pitched((size_t)D.plane, 0);
+    for (int y = 0; y < D.ny; ++y) memcpy(&pitched[(size_t)y * D.pitch], &hs[(size_t)y * D.nx], D.nx);
+    std::vector<uint16_t> fl;
+    std::vector<uint32_t> words;
+    build_flags(D, hs.data(), fl, words);
+    CKC(c, cudaMemcpy(c->solid + D.node_off, pitched.data(), pitched.size(), cudaMemcpyHostToDevice));
+    CKC(c, cudaMemcpy(c->nflags + D.node_off, fl.data(), fl.size() * 2, cudaMemcpyHostToDevice));
+    if (!words.empty())
+        CKC(c, cudaMemcpy(c->special + D.mask_off, words.data(), words.size() * 4, cudaMemcpyHostToDevice));
     return LBM_OK;
 }
 
@@ -391,6 +440,7 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
     CKCR(cudaMalloc(&c->f[0], c->arena_elems * c->esz));
     CKCR(cudaMalloc(&c->f[1], c->arena_elems * c->esz));
     CKCR(cudaMalloc(&c->solid, c->node_bytes));
+    CKCR(cudaMalloc(&c->nflags, c->node_bytes * 2));
     CKCR(cudaMalloc(&c->special, std::max<size_t>(1, c->special_words) * 4));
     CKCR(cudaMalloc(&c->dd, sizeof(DomDev) * ndom));
     CKCR(cudaMalloc(&c->d_item_off, sizeof(int64_t) * ndom));
@@ -405,7 +455,10 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
     CKCR(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
     CKCR(cudaMemcpyAsync(c->dd, c->hd.data(), sizeof(DomDev) * ndom, cudaMemcpyHostToDevice, c->stream));
     CKCR(cudaMemcpyAsync(c->d_item_off, item_off.data(), sizeof(int64_t) * ndom, cudaMemcpyHostToDevice, c->stream));
-    // special bits of an all-fluid geometry are zero; rest state in arena 0
+    CKCR(cudaStreamSynchronize(c->stream));
+    for (int d = 0; d < ndom; ++d)
+        if ((r = upload_geometry(c, d)) != LBM_OK) { g_create_error = c->msg; return cleanup(r); }
+    // rest state in arena 0
     CKCR(launch_fill_rest(c->kind, c->dd, ndom, c->hd.data(), c->f[0], c->solid, c->stream));
     if (c->np_slots > 0) {
         c->hst.assign(c->np_slots, PartStatic{});
@@ -425,7 +478,7 @@ void lbm_destroy(lbm_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& g : c->gexec)
         if (g) cudaGraphExecDestroy(g);
-    cudaFree(c->f[0]); cudaFree(c->f[1]); cudaFree(c->solid); cudaFree(c->special);
+    cudaFree(c->f[0]); cudaFree(c->f[1]); cudaFree(c->solid); cudaFree(c->nflags); cudaFree(c->special);
     cudaFree(c->dd); cudaFree(c->d_item_off); cudaFree(c->ctr); cudaFree(c->err);
     cudaFree(c->d_partial); cudaFree(c->d_sums); cudaFree(c->d_stage); cudaFree(c->d_mom);
     if (c->h_mom) cudaFreeHost(c->h_mom);
@@ -446,14 +499,9 @@ int lbm_set_geometry(lbm_ctx* c, int dom, const uint8_t* solid) {
     const DomDev& D = c->hd[dom];
     std::vector<uint8_t>& hs = c->hsolid[dom];
     for (size_t k = 0; k < hs.size(); ++k) hs[k] = solid[k] ? 1 : 0;
-    std::vector<uint8_t> pitched((size_t)D.plane, 0);
-    for (int y = 0; y < D.ny; ++y) memcpy(&pitched[(size_t)y * D.pitch], &hs[(size_t)y * D.nx], D.nx);
-    std::vector<uint32_t> words;
-    build_special(D, hs.data(), words);
     CKC(c, cudaStreamSynchronize(c->stream));
-    CKC(c, cudaMemcpy(c->solid + D.node_off, pitched.data(), pitched.size(), cudaMemcpyHostToDevice));
-    if (!words.empty())
-        CKC(c, cudaMemcpy(c->special + D.mask_off, words.data(), words.size() * 4, cudaMemcpyHostToDevice));
+    r = upload_geometry(c, dom);
+    if (r) return r;
     // solid nodes hold no populations: re-apply the current state with zeros there
     r = ensure_stage(c, sizeof(double) * 9 * (size_t)D.nx * D.ny);
     if (r) return r;

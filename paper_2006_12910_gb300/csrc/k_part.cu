@@ -56,6 +56,61 @@ __device__ __forceinline__ bool wrap_node(const DomDev& D, int& x, int& y) {
     return true;
 }
 
+// Box of lattice nodes around a disk, in unwrapped coordinates.
+struct Box {
+    int x0, y0, w, h;
+    __device__ int n() const { return w * h; }
+};
+__device__ __forceinline__ Box disk_box(double px, double py, double R) {
+    Box b;
+    b.x0 = (int)floor(px - R) - 1;
+    b.y0 = (int)floor(py - R) - 1;
+    b.w = (int)ceil(px + R) + 1 - b.x0 + 1;
+    b.h = (int)ceil(py + R) + 1 - b.y0 + 1;
+    return b;
+}
+
+// Inside test of node (xu, yu) (unwrapped, near the disk).  An FP32 distance
+// decides when it is clear of the rim by more than its error bound; within
+// that margin the exact FP64 evaluation (wrapped coordinates when `wrapped`,
+// as the rasterisation uses, unwrapped otherwise) decides, so the answer is
+// always that of the plain FP64 test.
+struct DiskF {
+    double px, py, R;
+    int cx, cy;
+    float fx, fy, R2, margin;
+};
+__device__ __forceinline__ DiskF make_diskf(double px, double py, double R) {
+    DiskF d;
+    d.px = px; d.py = py; d.R = R;
+    d.cx = (int)floor(px); d.cy = (int)floor(py);
+    d.fx = (float)(px - d.cx); d.fy = (float)(py - d.cy);
+    d.R2 = (float)(R * R);
+    d.margin = 1e-3f * fmaxf(1.0f, d.R2 * 0.01f) + 1e-4f;
+    return d;
+}
+// Integer minimum image of a node offset along a periodic axis.
+__device__ __forceinline__ int wrap_off(int d, int L, bool periodic) {
+    if (!periodic) return d;
+    d %= L;
+    if (d < 0) d += L;
+    if (2 * d >= L) d -= L;
+    return d;
+}
+__device__ __forceinline__ bool inside_f(const DomDev& D, const DiskF& k, int xu, int yu, bool wrapped) {
+    const int dxi = wrap_off(xu - k.cx, D.nx, D.flags & FLAG_PX), dyi = wrap_off(yu - k.cy, D.ny, D.flags & FLAG_PY);
+    const float dx = (float)dxi - k.fx, dy = (float)dyi - k.fy;
+    const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    if (d2 < k.R2 - k.margin) return true;
+    if (d2 > k.R2 + k.margin) return false;
+    if (wrapped) {
+        int x = xu, y = yu;
+        if (!wrap_node(D, x, y)) { x = xu; y = yu; }
+        return inside_disk(D, k.px, k.py, k.R, x, y);
+    }
+    return inside_disk(D, k.px, k.py, k.R, xu, yu);
+}
+
 template <class S>
 __device__ __forceinline__ double full_pop(const typename S::T* base, const DomDev& D, int i, int64_t ni) {
     const double v = (double)to_a(base[(int64_t)i * D.plane + ni], (typename S::A)D.inv_scale);
@@ -100,6 +155,57 @@ __device__ __forceinline__ int block_scan(int c, int* sh_warp, int& excl) {
     return total;
 }
 
+constexpr int PB_CAP = 4096;   // nodes of a shared-memory inside bitmap
+constexpr int LJ_MAXOFF = 128;  // offsets within the LJ threshold held in shared memory
+constexpr int MAXNEAR = 64;     // nearby particles considered per particle
+
+// Exclusive block scan of small non-negative counts; returns the block total.
+__device__ __forceinline__ int block_scan(int c, int* sh_warp, int& excl);
+
+// Other particles of the domain whose disks come within `extra` of the disk
+// (x, y, R), in index order, with their FP32 test data.  Every thread tests
+// its share of the particles; a block scan compacts the list, so the order is
+// fixed and no thread walks the particle array alone.
+__device__ __forceinline__ void near_list(const PartArgs& a, const DomDev& D, int p, const PartState* states,
+                                          double x, double y, double R, double extra, int* list, DiskF* disks,
+                                          int* count, int* sh_warp) {
+    int total = 0;
+    for (int b0 = 0; b0 < D.np; b0 += PBLOCK) {
+        const int j = b0 + (int)threadIdx.x;
+        const int p2 = D.p0 + j;
+        int hit = 0;
+        PartState o;
+        double r2 = 0.0;
+        if (j < D.np && p2 != p) {
+            o = states[p2];
+            r2 = a.st[p2].R;
+            const double dx = min_image(o.x - x, D.nx, D.flags & FLAG_PX);
+            const double dy = min_image(o.y - y, D.ny, D.flags & FLAG_PY);
+            const double reach = R + r2 + extra;
+            hit = dx * dx + dy * dy <= reach * reach;
+        }
+        int excl;
+        const int tot = block_scan(hit, sh_warp, excl);
+        if (hit && total + excl < MAXNEAR) {
+            list[total + excl] = p2;
+            disks[total + excl] = make_diskf(o.x, o.y, r2);
+        }
+        total += tot;
+    }
+    if (threadIdx.x == 0) *count = total;
+    __syncthreads();
+}
+
+// Surface node of a disk (inside, with an 8-neighbour outside), unwrapped
+// coordinates near the disk, using the FP32 test with its exact fallback.
+__device__ __forceinline__ bool is_surface_f(const DomDev& D, const DiskF& k, int x, int y) {
+    if (!inside_f(D, k, x, y, false)) return false;
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+        if (!inside_f(D, k, x + cx(i), y + cy(i), false)) return true;
+    return false;
+}
+
 template <class S>
 __global__ void __launch_bounds__(PBLOCK) k_particle_forces(PartArgs a) {
     const int p = blockIdx.x;
@@ -111,6 +217,14 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_forces(PartArgs a) {
     const typename S::T* base = static_cast<const typename S::T*>(a.arena) + D.off;
     const bool px = D.flags & FLAG_PX, py = D.flags & FLAG_PY;
     __shared__ double sh[DIAG_N][PBLOCK];
+    __shared__ uint8_t bm[PB_CAP];
+    __shared__ double lj_fx[LJ_MAXOFF], lj_fy[LJ_MAXOFF];
+    __shared__ int lj_ox[LJ_MAXOFF], lj_oy[LJ_MAXOFF];
+    __shared__ uint8_t lj_ok[LJ_MAXOFF];
+    __shared__ int lj_n, nnear;
+    __shared__ int sh_warp[PBLOCK / 32];
+    __shared__ int near[MAXNEAR];
+    __shared__ DiskF near_d[MAXNEAR];
 
     double acc[DIAG_N];
 #pragma unroll
@@ -168,56 +282,89 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_forces(PartArgs a) {
     // solid / wall nodes, within the threshold r_it.
     if (D.lj_psi != 0.0) {
         const double R = st.R;
-        const int bx0 = (int)floor(q.x - R) - 1, bx1 = (int)ceil(q.x + R) + 1;
-        const int by0 = (int)floor(q.y - R) - 1, by1 = (int)ceil(q.y + R) + 1;
-        const int bw = bx1 - bx0 + 1, bn = bw * (by1 - by0 + 1);
+        const Box b = disk_box(q.x, q.y, R);
+        const Box e = {b.x0 - 1, b.y0 - 1, b.w + 2, b.h + 2};
         const int reach = (int)floor(D.lj_rit);
-        for (int t = threadIdx.x; t < bn; t += PBLOCK) {
-            const int ay = by0 + t / bw, ax = bx0 + t % bw;
-            if (!is_surface(D, q.x, q.y, R, ax, ay)) continue;
-            const double rax = min_image(ax - q.x, D.nx, px), ray = min_image(ay - q.y, D.ny, py);
-            for (int p2 = D.p0; p2 < D.p0 + D.np; ++p2) {
-                if (p2 == p) continue;
-                const PartState o = a.cur[p2];
-                const double oR = a.st[p2].R;
-                const double cdx = min_image(o.x - q.x, D.nx, px), cdy = min_image(o.y - q.y, D.ny, py);
-                const double reachc = R + oR + D.lj_rit + 4.0;
-                if (cdx * cdx + cdy * cdy > reachc * reachc) continue;
-                const int ox0 = (int)floor(o.x - oR) - 1, ox1 = (int)ceil(o.x + oR) + 1;
-                const int oy0 = (int)floor(o.y - oR) - 1, oy1 = (int)ceil(o.y + oR) + 1;
-                for (int by = oy0; by <= oy1; ++by)
-                    for (int bx = ox0; bx <= ox1; ++bx) {
-                        if (!is_surface(D, o.x, o.y, oR, bx, by)) continue;
-                        const double sx = min_image((double)(ax - bx), D.nx, px);
-                        const double sy = min_image((double)(ay - by), D.ny, py);
-                        const double dist = sqrt(sx * sx + sy * sy);
-                        if (!(dist <= D.lj_rit) || dist == 0.0) continue;
-                        const double mag = D.lj_psi * pow(dist / D.lj_rit, -13.0);
-                        const double Fx = mag * sx / dist, Fy = mag * sy / dist;
-                        acc[6] += Fx;
-                        acc[7] += Fy;
-                        acc[8] += rax * Fy - ray * Fx;
-                    }
+        const bool use_bm = e.n() <= PB_CAP;
+        // Offset table of the pair force within r_it: entry t holds offset
+        // (t % w - reach, t / w - reach) and psi (d/r_it)^-13 (-o)/d, or zero.
+        const int ow = 2 * reach + 1;
+        if (threadIdx.x == 0) lj_n = ow * ow <= LJ_MAXOFF ? ow * ow : LJ_MAXOFF;
+        for (int t = threadIdx.x; t < ow * ow && t < LJ_MAXOFF; t += PBLOCK) {
+            const int ox = t % ow - reach, oy = t / ow - reach;
+            const double dist = sqrt((double)(ox * ox + oy * oy));
+            lj_ox[t] = ox;
+            lj_oy[t] = oy;
+            if ((ox == 0 && oy == 0) || !(dist <= D.lj_rit)) {
+                lj_ok[t] = 0;
+                lj_fx[t] = 0.0;
+                lj_fy[t] = 0.0;
+            } else {
+                const double x1 = dist / D.lj_rit, x2 = x1 * x1, x4 = x2 * x2, x8 = x4 * x4;
+                const double mag = D.lj_psi / (x8 * x4 * x1);
+                lj_ok[t] = 1;
+                lj_fx[t] = -mag * ox / dist;
+                lj_fy[t] = -mag * oy / dist;
             }
-            for (int oy = -reach; oy <= reach; ++oy)
-                for (int ox = -reach; ox <= reach; ++ox) {
-                    if (ox == 0 && oy == 0) continue;
-                    const double dist = sqrt((double)(ox * ox + oy * oy));
-                    if (!(dist <= D.lj_rit)) continue;
-                    int wx = ax + ox, wy = ay + oy;
-                    bool wall;
-                    if ((D.flags & FLAG_WY) && (wy < 0 || wy >= D.ny)) wall = true;
-                    else {
-                        if (!wrap_node(D, wx, wy)) continue;
-                        wall = a.solid[D.node_off + (int64_t)wy * D.pitch + wx] != 0;
-                    }
-                    if (!wall) continue;
-                    const double mag = D.lj_psi * pow(dist / D.lj_rit, -13.0);
-                    const double Fx = -mag * ox / dist, Fy = -mag * oy / dist;
-                    acc[6] += Fx;
-                    acc[7] += Fy;
-                    acc[8] += rax * Fy - ray * Fx;
+        }
+        near_list(a, D, p, a.cur, q.x, q.y, R, D.lj_rit + 4.0, near, near_d, &nnear, sh_warp);
+        if (use_bm) {
+            const DiskF kf = make_diskf(q.x, q.y, R);
+            for (int t = threadIdx.x; t < e.n(); t += PBLOCK)
+                bm[t] = inside_f(D, kf, e.x0 + t % e.w, e.y0 + t / e.w, false) ? 1 : 0;
+        }
+        __syncthreads();
+        const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
+        for (int t = threadIdx.x; t < b.n(); t += PBLOCK) {
+            const int ay = b.y0 + t / b.w, ax = b.x0 + t % b.w;
+            bool surf;
+            if (use_bm) {
+                const int c = (ay - e.y0) * e.w + (ax - e.x0);
+                surf = bm[c] != 0;
+                if (surf) {
+                    bool all_in = true;
+#pragma unroll
+                    for (int i = 1; i < 9; ++i) all_in &= bm[c + cy(i) * e.w + cx(i)] != 0;
+                    surf = !all_in;
                 }
+            } else {
+                surf = is_surface(D, q.x, q.y, R, ax, ay);
+            }
+            if (!surf) continue;
+            const double rax = min_image(ax - q.x, D.nx, px), ray = min_image(ay - q.y, D.ny, py);
+            for (int j = 0; j < nn; ++j) {
+                const DiskF& ko = near_d[j];
+                // only surface nodes of p within r_it of the other disk's rim can pair
+                const float ddx = (float)wrap_off(ax - ko.cx, D.nx, px) - ko.fx;
+                const float ddy = (float)wrap_off(ay - ko.cy, D.ny, py) - ko.fy;
+                const float lim = (float)(ko.R + D.lj_rit) + 2.0f;
+                if (ddx * ddx + ddy * ddy > lim * lim) continue;
+                for (int w = 0; w < lj_n; ++w) {
+                    if (!lj_ok[w]) continue;
+                    // node b = a + o expressed in the other particle's own frame
+                    const int bx = ko.cx + wrap_off(ax + lj_ox[w] - ko.cx, D.nx, px);
+                    const int by = ko.cy + wrap_off(ay + lj_oy[w] - ko.cy, D.ny, py);
+                    if (!is_surface_f(D, ko, bx, by)) continue;
+                    // repulsion on a from b = a + o: psi (d/r_it)^-13 (a - b)/d, the table entry of o
+                    acc[6] += lj_fx[w];
+                    acc[7] += lj_fy[w];
+                    acc[8] += rax * lj_fy[w] - ray * lj_fx[w];
+                }
+            }
+            for (int j = 0; j < lj_n; ++j) {
+                if (!lj_ok[j]) continue;
+                int wx = ax + lj_ox[j], wy = ay + lj_oy[j];
+                bool wall;
+                if ((D.flags & FLAG_WY) && (wy < 0 || wy >= D.ny)) wall = true;
+                else {
+                    if (!wrap_node(D, wx, wy)) continue;
+                    wall = a.solid[D.node_off + (int64_t)wy * D.pitch + wx] != 0;
+                }
+                if (!wall) continue;
+                acc[6] += lj_fx[j];
+                acc[7] += lj_fy[j];
+                acc[8] += rax * lj_fy[j] - ray * lj_fx[j];
+            }
         }
     }
 
@@ -256,6 +403,10 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_links(PartArgs a, int swap,
     typename S::T* base = static_cast<typename S::T*>(a.arena) + D.off;
     const bool px = D.flags & FLAG_PX, py = D.flags & FLAG_PY;
     __shared__ int sh_warp[PBLOCK / 32];
+    __shared__ uint8_t bnew[PB_CAP], bold[PB_CAP];
+    __shared__ int near[MAXNEAR];
+    __shared__ DiskF near_d[MAXNEAR];
+    __shared__ int nnear;
 
     // Eqs. MP7-MP8 on the links of the rasterisation at t with u_b(t).
     if (swap) {
@@ -281,90 +432,98 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_links(PartArgs a, int swap,
     }
 
     const PartState n = advance ? a.next[p] : q;
+    const PartState* others = advance ? a.next : a.cur;
     const double R = st.R;
-    // New link list at the new position.
-    {
-        const int bx0 = (int)floor(n.x - R) - 1, bx1 = (int)ceil(n.x + R) + 1;
-        const int by0 = (int)floor(n.y - R) - 1, by1 = (int)ceil(n.y + R) + 1;
-        const int bw = bx1 - bx0 + 1, bn = bw * (by1 - by0 + 1);
-        int total = 0;
-        bool overlap = false;
-        for (int t0 = 0; t0 < bn; t0 += PBLOCK) {
-            const int t = t0 + threadIdx.x;
-            uint32_t mask = 0;
-            int node = 0;
-            if (t < bn) {
-                int x = bx0 + t % bw, y = by0 + t / bw;
-                if (wrap_node(D, x, y) && inside_disk(D, n.x, n.y, R, x, y)) {
-                    node = y * D.pitch + x;
-                    for (int p2 = D.p0; p2 < D.p0 + D.np; ++p2) {
-                        if (p2 == p) continue;
-                        const PartState o = advance ? a.next[p2] : a.cur[p2];
-                        if (inside_disk(D, o.x, o.y, a.st[p2].R, x, y)) overlap = true;
-                    }
-                    if (!a.solid[D.node_off + node]) {
+    // Union of the old and new boxes; every neighbour of a node inside either
+    // disk lies in it.
+    const Box bo = disk_box(q.x, q.y, R), bn = disk_box(n.x, n.y, R);
+    Box U;
+    U.x0 = min(bo.x0, bn.x0);
+    U.y0 = min(bo.y0, bn.y0);
+    U.w = max(bo.x0 + bo.w, bn.x0 + bn.w) - U.x0;
+    U.h = max(bo.y0 + bo.h, bn.y0 + bn.h) - U.y0;
+    const bool use_bm = U.n() <= PB_CAP;
+    near_list(a, D, p, others, n.x, n.y, R, 4.0, near, near_d, &nnear, sh_warp);
+    const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
+    if (nnear > MAXNEAR && threadIdx.x == 0) atomicOr(a.err, ERR_STATE);
+    if (use_bm) {
+        const DiskF kn = make_diskf(n.x, n.y, R), ko = make_diskf(q.x, q.y, R);
+        for (int t = threadIdx.x; t < U.n(); t += PBLOCK) {
+            const int xu = U.x0 + t % U.w, yu = U.y0 + t / U.w;
+            bnew[t] = inside_f(D, kn, xu, yu, true) ? 1 : 0;
+            bold[t] = advance ? (inside_f(D, ko, xu, yu, true) ? 1 : 0) : bnew[t];
+        }
+    }
+    __syncthreads();
+    auto in_new = [&](int xu, int yu) -> bool {
+        if (use_bm) return bnew[(yu - U.y0) * U.w + (xu - U.x0)] != 0;
+        int x = xu, y = yu;
+        if (!wrap_node(D, x, y)) { x = xu; y = yu; }
+        return inside_disk(D, n.x, n.y, R, x, y);
+    };
+    auto in_old = [&](int xu, int yu) -> bool {
+        if (use_bm) return bold[(yu - U.y0) * U.w + (xu - U.x0)] != 0;
+        int x = xu, y = yu;
+        if (!wrap_node(D, x, y)) { x = xu; y = yu; }
+        return inside_disk(D, q.x, q.y, R, x, y);
+    };
+
+    // New link list and nodes that changed side, in a fixed (row-major, lane) order.
+    int ltotal = 0, ftotal = 0;
+    bool overlap = false;
+    for (int t0 = 0; t0 < U.n(); t0 += PBLOCK) {
+        const int t = t0 + threadIdx.x;
+        uint32_t mask = 0;
+        int node = 0, fcode = 0, fc = 0;
+        if (t < U.n()) {
+            const int xu = U.x0 + t % U.w, yu = U.y0 + t / U.w;
+            int x = xu, y = yu;
+            if (wrap_node(D, x, y)) {
+                node = y * D.pitch + x;
+                const bool solid_here = a.solid[D.node_off + node] != 0;
+                const bool now = in_new(xu, yu);
+                if (now) {
+                    for (int j = 0; j < nn; ++j)
+                        if (inside_f(D, near_d[j], xu, yu, true)) overlap = true;
+                    if (!solid_here) {
 #pragma unroll
                         for (int k = 1; k < 9; ++k) {
-                            int fx = x + cx(k), fy = y + cy(k);
+                            const int fxu = xu + cx(k), fyu = yu + cy(k);
+                            int fx = fxu, fy = fyu;
                             if (!wrap_node(D, fx, fy)) continue;
                             if (a.solid[D.node_off + (int64_t)fy * D.pitch + fx]) continue;
-                            bool in_any = inside_disk(D, n.x, n.y, R, fx, fy);
-                            for (int p2 = D.p0; p2 < D.p0 + D.np && !in_any; ++p2) {
-                                if (p2 == p) continue;
-                                const PartState o = advance ? a.next[p2] : a.cur[p2];
-                                in_any = inside_disk(D, o.x, o.y, a.st[p2].R, fx, fy);
-                            }
+                            bool in_any = in_new(fxu, fyu);
+                            for (int j = 0; j < nn && !in_any; ++j) in_any = inside_f(D, near_d[j], fxu, fyu, true);
                             if (!in_any) mask |= 1u << k;
                         }
                     }
                 }
-            }
-            int excl;
-            const int c = __popc(mask);
-            const int tot = block_scan(c, sh_warp, excl);
-            int w = total + excl;
-            for (int k = 1; k < 9; ++k)
-                if (mask & (1u << k)) {
-                    if (w < st.link_cap) a.links[st.link_off + w] = (node << 3) | (k - 1);
-                    ++w;
+                if (advance && !solid_here && now != in_old(xu, yu)) {
+                    fc = 1;
+                    fcode = (node << 1) | (now ? 1 : 0);
                 }
-            total += tot;
+            }
         }
-        if (overlap || total > st.link_cap) atomicOr(a.err, ERR_STATE);
-        if (threadIdx.x == 0) a.nlinks[p] = total < st.link_cap ? total : st.link_cap;
+        int excl;
+        const int c = __popc(mask);
+        const int tot = block_scan(c, sh_warp, excl);
+        int w = ltotal + excl;
+        for (int k = 1; k < 9; ++k)
+            if (mask & (1u << k)) {
+                if (w < st.link_cap) a.links[st.link_off + w] = (node << 3) | (k - 1);
+                ++w;
+            }
+        ltotal += tot;
+        int fex;
+        const int ftot = block_scan(fc, sh_warp, fex);
+        if (fc && ftotal + fex < st.flip_cap) a.flips[st.flip_off + ftotal + fex] = fcode;
+        ftotal += ftot;
     }
-    // Nodes that change side between the old and the new position.
-    {
-        const int bx0 = (int)floor(fmin(q.x, n.x) - R) - 1, bx1 = (int)ceil(fmax(q.x, n.x) + R) + 1;
-        const int by0 = (int)floor(fmin(q.y, n.y) - R) - 1, by1 = (int)ceil(fmax(q.y, n.y) + R) + 1;
-        const int bw = bx1 - bx0 + 1, bn = bw * (by1 - by0 + 1);
-        int total = 0;
-        for (int t0 = 0; t0 < bn; t0 += PBLOCK) {
-            const int t = t0 + threadIdx.x;
-            int c = 0, code = 0;
-            if (t < bn && advance) {
-                int x = bx0 + t % bw, y = by0 + t / bw;
-                if (wrap_node(D, x, y)) {
-                    // the union box stays far below the domain size, so a
-                    // wrapped node is visited once
-                    const int node = y * D.pitch + x;
-                    const bool was = inside_disk(D, q.x, q.y, R, x, y), now = inside_disk(D, n.x, n.y, R, x, y);
-                    if (was != now && !a.solid[D.node_off + node]) { c = 1; code = (node << 1) | (now ? 1 : 0); }
-                }
-            }
-            int excl;
-            const int tot = block_scan(c, sh_warp, excl);
-            if (c) {
-                const int w = total + excl;
-                if (w < st.flip_cap) a.flips[st.flip_off + w] = code;
-            }
-            total += tot;
-        }
-        if (total > st.flip_cap) atomicOr(a.err, ERR_STATE);
-        if (threadIdx.x == 0) {
-            a.nflips[p] = total < st.flip_cap ? total : st.flip_cap;
-            if (advance) a.cur[p] = n;
-        }
+    if (overlap || ltotal > st.link_cap || ftotal > st.flip_cap) atomicOr(a.err, ERR_STATE);
+    if (threadIdx.x == 0) {
+        a.nlinks[p] = ltotal < st.link_cap ? ltotal : st.link_cap;
+        a.nflips[p] = ftotal < st.flip_cap ? ftotal : st.flip_cap;
+        if (advance) a.cur[p] = n;
     }
 }
 

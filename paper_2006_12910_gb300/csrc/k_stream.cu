@@ -11,9 +11,12 @@
 // extra element at the chunk edge (served by L1 from the neighbour lane's
 // sector), then collides in registers and writes 16-byte vectors.
 //
-// Chunks touching an x edge, a wall row, a solid node or a solid neighbour
-// (flagged in a per-row bitmask written once from the geometry) take a
-// per-node path with explicit boundary logic and scalar accesses.
+// Chunks that touch a wall, a solid, an open column or a periodic seam are
+// flagged in a per-row bitmask; they read the per-node flag words and patch
+// the pulled vectors in registers (bounce-back from the node's own opposite
+// slot, Zou-He on the open columns), so they stay on the same vector path.
+// Only the ragged last chunk of a row whose width is no multiple of V takes
+// a scalar per-node path.
 #include "kernels.h"
 #include "lbm_dev.cuh"
 
@@ -28,17 +31,17 @@ __device__ __forceinline__ int find_domain(const int64_t* __restrict__ item_off,
     return lo;
 }
 
-// Per-node path: pull with halfway bounce-back at walls / solids, wall-corner
-// reflection and Zou-He on the open columns, then collide and store scalars.
+// Scalar per-node path for the ragged tail: pull with halfway bounce-back at
+// walls / solids, wall-corner reflection and Zou-He on the open columns.
 template <class S, bool NOISE, bool PL>
-__device__ __forceinline__ bool slow_node(const DomDev& D, int x, int y, const typename S::T* __restrict__ base,
-                                          typename S::T* __restrict__ obase, const uint8_t* __restrict__ solid,
-                                          uint32_t step) {
+__device__ __noinline__ bool slow_node(const DomDev& D, const Prm<typename S::A>& P, int x, int y,
+                                       const typename S::T* __restrict__ base, typename S::T* __restrict__ obase,
+                                       const uint8_t* __restrict__ solid, uint32_t step) {
     typedef typename S::A A;
     const int nx = D.nx, ny = D.ny, pitch = D.pitch, flags = D.flags;
     const int64_t ni = (int64_t)y * pitch + x;
     if (__ldg(solid + D.node_off + ni)) return true;  // solid nodes hold no populations
-    const A inv = (A)D.inv_scale;
+    const A inv = P.inv_scale;
     const bool corner_row = (flags & FLAG_WY) && (y == 0 || y == ny - 1);
     A f[9];
 #pragma unroll
@@ -60,14 +63,30 @@ __device__ __forceinline__ bool slow_node(const DomDev& D, int x, int y, const t
         else f[i] = load_one<S>(base + (int64_t)i * D.plane + (int64_t)sy * pitch + sx, inv);
     }
     if ((flags & FLAG_IO) && !corner_row && (x == 0 || x == nx - 1)) {
-        if (x == 0) zou_he<A>(f, 0, (A)D.rho_in, S::SHIFT ? (A)D.drho_in : (A)D.rho_in);
-        else zou_he<A>(f, 1, (A)D.rho_out, S::SHIFT ? (A)D.drho_out : (A)D.rho_out);
+        if (x == 0) zou_he<A>(f, 0, P.rho_in, P.d_in);
+        else zou_he<A>(f, 1, P.rho_out, P.d_out);
     }
-    const bool ok = collide_node<A, S::SHIFT, NOISE, PL>(f, D, (uint32_t)((int64_t)y * nx + x), step);
-    const A scl = (A)D.scale;
+    const bool ok = collide_node<A, S::SHIFT, NOISE, PL>(f, P, (uint32_t)((int64_t)y * nx + x), step);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) from_a(f[i], scl, obase[(int64_t)i * D.plane + ni]);
+    for (int i = 0; i < 9; ++i) from_a(f[i], P.scale, obase[(int64_t)i * D.plane + ni]);
     return ok;
+}
+
+// V per-node flag words of one chunk (V*2 bytes, aligned).
+template <int V>
+__device__ __forceinline__ void load_flags(const uint16_t* p, uint16_t (&fl)[V]) {
+    if constexpr (V == 2) {
+        const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(p));
+        fl[0] = (uint16_t)w; fl[1] = (uint16_t)(w >> 16);
+    } else if constexpr (V == 4) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2*>(p));
+        fl[0] = (uint16_t)w.x; fl[1] = (uint16_t)(w.x >> 16); fl[2] = (uint16_t)w.y; fl[3] = (uint16_t)(w.y >> 16);
+    } else {
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(p));
+        const uint32_t a[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { fl[2 * k] = (uint16_t)a[k]; fl[2 * k + 1] = (uint16_t)(a[k] >> 16); }
+    }
 }
 
 template <class S, bool NOISE, bool PL>
@@ -87,61 +106,97 @@ __global__ void __launch_bounds__(512) k_stream_collide(StreamArgs a) {
     for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < a.total_items; g += nwarps) {
         const int d = a.ndom == 1 ? 0 : find_domain(a.item_off, a.ndom, g);
         const DomDev& D = a.doms[d];
+        const int nx = D.nx, ny = D.ny, flags = D.flags;
+        const int64_t pitch = D.pitch, plane = D.plane;
         const int local = (int)(g - D.item_off);
         const int y = local / D.seg_per_row;
         const int seg = local - y * D.seg_per_row;
         const int x0 = (seg * 32 + lane) * V;
         const uint32_t word = __ldg(a.special + D.mask_off + (int64_t)y * D.seg_per_row + seg);
-        const int nx = D.nx, ny = D.ny;
         if (x0 >= nx) continue;
+        const Prm<A> P = load_prm<A>(D);
         const T* base = src + D.off;
         T* obase = dst + D.off;
-        const bool special = (word >> lane) & 1u;
-        const bool edge_x = (x0 == 0) || (x0 + V >= nx);
-        const bool edge_y = (D.flags & FLAG_WY) && (y == 0 || y == ny - 1);
-        if (special || edge_x || edge_y) {
+        if (x0 + V > nx) {  // ragged tail chunk
 #pragma unroll 1
             for (int k = 0; k < V; ++k)
-                if (x0 + k < nx) ok &= slow_node<S, NOISE, PL>(D, x0 + k, y, base, obase, a.solid, step);
+                if (x0 + k < nx) ok &= slow_node<S, NOISE, PL>(D, P, x0 + k, y, base, obase, a.solid, step);
             continue;
         }
-        // Fast path: interior chunk, no solid anywhere near, rows in range or periodic.
-        const A inv = (A)D.inv_scale;
-        const int ym = y == 0 ? ny - 1 : y - 1;
-        const int yp = y == ny - 1 ? 0 : y + 1;
-        const int64_t pitch = D.pitch, plane = D.plane;
+        const A inv = P.inv_scale;
+        int ym = y - 1, yp = y + 1;
+        if (ym < 0) ym = (flags & FLAG_PY) ? ny - 1 : y;   // a wall row pulls nothing from row -1
+        if (yp >= ny) yp = (flags & FLAG_PY) ? 0 : y;
+        int xl = x0 - 1, xr = x0 + V;
+        if (xl < 0) xl = (flags & FLAG_PX) ? nx - 1 : 0;  // open ends: placeholder, patched below
+        if (xr >= nx) xr = (flags & FLAG_PX) ? xr - nx : nx - 1;
         A f[9][V];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int row = cy(i) == 1 ? ym : (cy(i) == -1 ? yp : y);
-            const T* p = base + (int64_t)i * plane + row * pitch + x0;
+            const T* p = base + (int64_t)i * plane + row * pitch;
             A v[V];
-            load_vec<S>(p, v, inv);
+            load_vec<S>(p + x0, v, inv);
             if (cx(i) == 0) {
 #pragma unroll
                 for (int k = 0; k < V; ++k) f[i][k] = v[k];
             } else if (cx(i) == 1) {  // source x-1
-                f[i][0] = load_one<S>(p - 1, inv);
+                f[i][0] = load_one<S>(p + xl, inv);
 #pragma unroll
                 for (int k = 1; k < V; ++k) f[i][k] = v[k - 1];
             } else {  // source x+1
 #pragma unroll
                 for (int k = 0; k < V - 1; ++k) f[i][k] = v[k + 1];
-                f[i][V - 1] = load_one<S>(p + V, inv);
+                f[i][V - 1] = load_one<S>(p + xr, inv);
             }
+        }
+        uint32_t solid_bits = 0;
+        if ((word >> lane) & 1u) {
+            uint16_t fl[V];
+            load_flags<V>(a.nflags + D.node_off + (int64_t)y * pitch + x0, fl);
+            uint32_t any = 0;
+#pragma unroll
+            for (int k = 0; k < V; ++k) any |= fl[k];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                if (any & (1u << i)) {  // halfway bounce-back: the node's own opposite slot
+                    A own[V];
+                    load_vec<S>(base + (int64_t)opp(i) * plane + y * pitch + x0, own, inv);
+#pragma unroll
+                    for (int k = 0; k < V; ++k)
+                        if (fl[k] & (1u << i)) f[i][k] = own[k];
+                }
+            }
+            if (any & (NF_ZH_IN | NF_ZH_OUT)) {
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    if (fl[k] & (NF_ZH_IN | NF_ZH_OUT)) {
+                        A n9[9];
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) n9[i] = f[i][k];
+                        if (fl[k] & NF_ZH_IN) zou_he<A>(n9, 0, P.rho_in, P.d_in);
+                        else zou_he<A>(n9, 1, P.rho_out, P.d_out);
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) f[i][k] = n9[i];
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                if (fl[k] & NF_SOLID) solid_bits |= 1u << k;
         }
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             A n9[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) n9[i] = f[i][k];
-            ok &= collide_node<A, S::SHIFT, NOISE, PL>(n9, D, (uint32_t)(y * nx + x0 + k), step);
+            const bool sol = (solid_bits >> k) & 1u;
+            if (!sol) ok &= collide_node<A, S::SHIFT, NOISE, PL>(n9, P, (uint32_t)(y * nx + x0 + k), step);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) f[i][k] = n9[i];
+            for (int i = 0; i < 9; ++i) f[i][k] = sol ? (A)0 : n9[i];
         }
-        const A scl = (A)D.scale;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) store_vec<S>(obase + (int64_t)i * plane + y * pitch + x0, f[i], scl);
+        for (int i = 0; i < 9; ++i) store_vec<S>(obase + (int64_t)i * plane + y * pitch + x0, f[i], P.scale);
     }
     if (!ok) atomicOr(a.err, ERR_UNSTABLE);
 }

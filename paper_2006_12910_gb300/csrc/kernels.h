@@ -15,8 +15,9 @@ struct StreamArgs {
     int64_t total_items;      // sum over domains of ny * seg_per_row
     const void* src;          // population arena holding f*(t) (after link swaps)
     void* dst;                // population arena receiving f*(t+1)
-    const uint8_t* solid;     // per-node solid bytes
-    const uint32_t* special;  // per-chunk slow-path bits
+    const uint8_t* solid;     // per-node solid bytes (ragged tail path)
+    const uint16_t* nflags;   // per-node flag words (NF_* and bounce-back bits)
+    const uint32_t* special;  // per-chunk bits: the chunk has a node with nonzero flags
     const int64_t* ctr_in;    // step counter of the source state
     int64_t* ctr_out;         // step counter of the destination state
     unsigned* err;            // sticky device error bits

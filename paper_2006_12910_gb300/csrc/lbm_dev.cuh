@@ -154,6 +154,40 @@ __device__ __forceinline__ void thetas(uint32_t node, uint32_t step, uint32_t do
 }
 
 // ---------------------------------------------------------------------------
+// Per-domain parameters in the arithmetic type, loaded once per work item so
+// the collision never converts between FP64 and FP32.
+// ---------------------------------------------------------------------------
+template <typename A>
+struct Prm {
+    A tau, inv_tau, rho0, gx, gy, kT, n, xi, tmin, tmax, tmin_pow, tmax_pow;
+    A rho_in, rho_out, d_in, d_out, scale, inv_scale;
+    int n_is_one;
+    uint32_t dom_id;
+    uint64_t seed;
+};
+template <typename A> __device__ __forceinline__ Prm<A> load_prm(const DomDev& D);
+template <> __device__ __forceinline__ Prm<float> load_prm<float>(const DomDev& D) {
+    Prm<float> P;
+    P.tau = D.tau_f; P.inv_tau = D.inv_tau_f; P.rho0 = D.rho0_f; P.gx = D.gx_f; P.gy = D.gy_f; P.kT = D.kT_f;
+    P.n = D.n_pl_f; P.xi = D.xi_pl_f; P.tmin = D.tau_min_f; P.tmax = D.tau_max_f;
+    P.tmin_pow = D.tmin_pow_f; P.tmax_pow = D.tmax_pow_f;
+    P.rho_in = D.rho_in_f; P.rho_out = D.rho_out_f; P.d_in = D.drho_in_f; P.d_out = D.drho_out_f;
+    P.scale = D.scale_f; P.inv_scale = D.inv_scale_f;
+    P.n_is_one = D.n_is_one; P.dom_id = D.domain_id; P.seed = D.seed;
+    return P;
+}
+template <> __device__ __forceinline__ Prm<double> load_prm<double>(const DomDev& D) {
+    Prm<double> P;
+    P.tau = D.tau; P.inv_tau = D.inv_tau; P.rho0 = D.rho0; P.gx = D.gx; P.gy = D.gy; P.kT = D.kT;
+    P.n = D.n_pl; P.xi = D.xi_pl; P.tmin = D.tau_min; P.tmax = D.tau_max;
+    P.tmin_pow = D.tmin_pow; P.tmax_pow = D.tmax_pow;
+    P.rho_in = D.rho_in; P.rho_out = D.rho_out; P.d_in = D.drho_in; P.d_out = D.drho_out;
+    P.scale = D.scale; P.inv_scale = D.inv_scale;
+    P.n_is_one = D.n_is_one; P.dom_id = D.domain_id; P.seed = D.seed;
+    return P;
+}
+
+// ---------------------------------------------------------------------------
 // Power-law relaxation time, Sec. 5.  The shear rate of Eq. nn2 with Pi_D of
 // Eq. nn3 taken from the Chapman-Enskog strain -Pi_neq / (2 rho c_s^2 tau) is
 // A / tau, A = 3 sqrt|Pi_xy^2 - Pi_xx Pi_yy| / rho; nu* = xi (A/tau)^(n-1)
@@ -166,17 +200,17 @@ template <> __device__ __forceinline__ float powa<float>(float x, float e) { ret
 template <> __device__ __forceinline__ double powa<double>(double x, double e) { return exp2(e * log2(x)); }
 
 template <typename A>
-__device__ __forceinline__ A solve_tau_pl(A Astr, const DomDev& D) {
-    const A n = (A)D.n_pl, tmin = (A)D.tau_min, tmax = (A)D.tau_max;
-    if (D.n_is_one) {
-        A t = (A)0.5 + (A)3.0 * (A)D.xi_pl;
+__device__ __forceinline__ A solve_tau_pl(A Astr, const Prm<A>& P) {
+    const A n = P.n, tmin = P.tmin, tmax = P.tmax;
+    if (P.n_is_one) {
+        A t = (A)0.5 + (A)3.0 * P.xi;
         return t < tmin ? tmin : (t > tmax ? tmax : t);
     }
     if (!(Astr > (A)0)) return n < (A)1 ? tmax : tmin;
     const A om = (A)1 - n;
-    const A c = (A)3.0 * (A)D.xi_pl * powa<A>(Astr, n - (A)1);
-    if (tmin - (A)0.5 - c * (A)D.tmin_pow >= (A)0) return tmin;
-    if (tmax - (A)0.5 - c * (A)D.tmax_pow <= (A)0) return tmax;
+    const A c = (A)3.0 * P.xi * powa<A>(Astr, n - (A)1);
+    if (tmin - (A)0.5 - c * P.tmin_pow >= (A)0) return tmin;
+    if (tmax - (A)0.5 - c * P.tmax_pow <= (A)0) return tmax;
     A t = n < (A)1 ? tmax : tmin;
     const A tol = sizeof(A) == 4 ? (A)2e-7 : (A)1e-15;
 #pragma unroll 1
@@ -201,18 +235,18 @@ __device__ __forceinline__ A solve_tau_pl(A Astr, const DomDev& D) {
 // Returns false when rho is not a positive finite number.
 // ---------------------------------------------------------------------------
 template <typename A, bool SHIFT, bool NOISE, bool PL>
-__device__ __forceinline__ bool collide_node(A f[9], const DomDev& D, uint32_t node, uint32_t step) {
+__device__ __forceinline__ bool collide_node(A f[9], const Prm<A>& P, uint32_t node, uint32_t step) {
     A s = f[0];
 #pragma unroll
     for (int i = 1; i < 9; ++i) s += f[i];
     const A jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     const A jy = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
-    const A rho0 = (A)D.rho0;
+    const A rho0 = P.rho0;
     const A rho = SHIFT ? rho0 + s : s;
     const A drho = SHIFT ? s : s - rho0;
     const bool ok = (rho > (A)0) && (rho < (A)1e30);
     const A irho = (A)1 / rho;
-    A tau = (A)D.tau, itau = (A)D.inv_tau;
+    A tau = P.tau, itau = P.inv_tau;
     if (PL) {
         const A sxx = (f[1] + f[3]) + (f[5] + f[6]) + (f[7] + f[8]);
         const A syy = (f[2] + f[4]) + (f[5] + f[6]) + (f[7] + f[8]);
@@ -221,13 +255,13 @@ __device__ __forceinline__ bool collide_node(A f[9], const DomDev& D, uint32_t n
         const A pxx = sxx - iso - jx * jx * irho;
         const A pyy = syy - iso - jy * jy * irho;
         const A pxy = sxy - jx * jy * irho;
-        const A P = pxy * pxy - pxx * pyy;
-        const A Astr = (A)3 * sqrt(fabs(P)) * irho;
-        tau = solve_tau_pl<A>(Astr, D);
+        const A det = pxy * pxy - pxx * pyy;
+        const A Astr = (A)3 * sqrt(fabs(det)) * irho;
+        tau = solve_tau_pl<A>(Astr, P);
         itau = (A)1 / tau;
     }
-    const A ux = (jx + tau * rho * (A)D.gx) * irho;
-    const A uy = (jy + tau * rho * (A)D.gy) * irho;
+    const A ux = (jx + tau * rho * P.gx) * irho;
+    const A uy = (jy + tau * rho * P.gy) * irho;
     const A usq = (A)1.5 * (ux * ux + uy * uy);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -237,10 +271,10 @@ __device__ __forceinline__ bool collide_node(A f[9], const DomDev& D, uint32_t n
         f[i] = f[i] + (feq - f[i]) * itau;
     }
     if (NOISE) {
-        if (D.kT > 0.0) {
+        if (P.kT > (A)0) {
             A th[6];
-            thetas<A>(node, step, D.domain_id, D.seed, th);
-            const A amp = sqrt(rho * (A)D.kT * itau * ((A)2 - itau) * (A)3);
+            thetas<A>(node, step, P.dom_id, P.seed, th);
+            const A amp = sqrt(rho * P.kT * itau * ((A)2 - itau) * (A)3);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 A z = (A)0;

@@ -19,7 +19,8 @@ enum : uint32_t {
 };
 
 // One lattice domain as the kernels see it.  Populations of plane i live at
-// arena[off + i*plane + y*pitch + x]; per-node bytes at nodes[node_off + y*pitch + x];
+// arena[off + i*plane + y*pitch + x]; per-node solid bytes and flag words at
+// nodes[node_off + y*pitch + x];
 // the special-chunk bitmask word of warp segment s of row y at
 // special[mask_off + y*seg_per_row + s] (bit = lane; a chunk is V nodes).
 struct DomDev {
@@ -36,6 +37,19 @@ struct DomDev {
     double n_pl, xi_pl, tau_min, tau_max, tmin_pow, tmax_pow;  // tmin^(1-n), tmax^(1-n)
     double lj_psi, lj_rit;
     double scale, inv_scale;  // store scale of the shifted FP16/BF16 kinds (1 otherwise)
+    // FP32 copies of the collision parameters, so the FP32 path converts nothing
+    float tau_f, inv_tau_f, rho0_f, gx_f, gy_f, rho_in_f, rho_out_f, drho_in_f, drho_out_f, kT_f;
+    float n_pl_f, xi_pl_f, tau_min_f, tau_max_f, tmin_pow_f, tmax_pow_f, scale_f, inv_scale_f;
+};
+
+// Per-node flag bits (uint16), written from the geometry on the host.  Bit i
+// (1..8): direction i is bounced back (its pull source is solid, beyond a
+// wall, or outside the x range at a wall-corner node).  A chunk whose nodes
+// all have zero flags takes the plain vector path without reading them.
+enum : uint16_t {
+    NF_SOLID = 1u << 0,
+    NF_ZH_IN = 1u << 9,    // Zou-He inlet node (x = 0)
+    NF_ZH_OUT = 1u << 10,  // Zou-He outlet node (x = nx - 1)
 };
 
 // Particle data on the device (Sec. 3).  State is double precision.
