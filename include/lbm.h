@@ -184,6 +184,32 @@ int lbm_autotune(lbm_ctx* ctx, int trial_steps);
  * advances exactly as with lbm_step. */
 int lbm_profile_steps(lbm_ctx* ctx, int64_t nsteps, double* ms_out3, int64_t* launches_out);
 
+/* Largest row count lbm_checks_noalloc accepts (its static scratch holds one
+ * FP64 triple per row). */
+#define LBM_NOALLOC_MAX_ROWS 16384
+
+/* The sums of lbm_checks over caller-owned device buffers, allocating nothing.
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not allocate device memory -- code running while a stream is captured,
+ * stepping loops that cannot take the device synchronisation of cudaMalloc /
+ * cudaFree, frameworks whose memory pool owns the GPU -- and so cannot create
+ * a context.  Inputs: d_populations = device populations of one domain in the
+ * library's layout, [9][ny][pitch] elements of the store type (lbm_store;
+ * shifted kinds hold (f_i - omega_i rho0) * store_scale), x fastest;
+ * d_solid = device bytes [ny][pitch], nonzero = solid (NULL: all fluid).
+ * Output: d_out3 = device double[3] receiving mass, sum f e_x, sum f e_y.
+ * Enqueued on cuda_stream (NULL: the legacy default stream); not blocking.
+ * Scratch is one static device array of LBM_NOALLOC_MAX_ROWS x 3 doubles
+ * (384 KiB on every GPU that loads the library, until exit); ny above that
+ * maximum is rejected with LBM_E_INVAL, as are bad sizes and a NULL buffer.
+ * The first call on a device looks up the array's device address (the runtime
+ * loads the module if it has not yet), so make that first call before any
+ * stream capture.  All calls share the array: calls whose kernels may overlap
+ * on the GPU must be ordered by the caller. */
+int lbm_checks_noalloc(const void* d_populations, int32_t store, int32_t nx, int32_t ny, int32_t pitch,
+                       double rho0, double store_scale, const uint8_t* d_solid, double* d_out3,
+                       void* cuda_stream);
+
 /* Last error message of the context (static string when ctx is NULL). */
 const char* lbm_last_error(const lbm_ctx* ctx);
 

@@ -25,8 +25,10 @@ EXPORTED = [
     "lbm_create", "lbm_create_ensemble", "lbm_set_geometry", "lbm_add_particles", "lbm_set_populations",
     "lbm_get_populations", "lbm_step", "lbm_sync", "lbm_moments", "lbm_moments_device", "lbm_moments_async",
     "lbm_moments_async_wait", "lbm_particles", "lbm_particle_forces", "lbm_checks", "lbm_step_count",
-    "lbm_save", "lbm_load", "lbm_autotune", "lbm_profile_steps", "lbm_last_error", "lbm_destroy",
+    "lbm_save", "lbm_load", "lbm_autotune", "lbm_profile_steps", "lbm_checks_noalloc", "lbm_last_error",
+    "lbm_destroy",
 ]
+NOALLOC_MAX_ROWS = 16384
 
 
 class LbmError(RuntimeError):
@@ -103,6 +105,8 @@ def load(build_if_missing: bool = True):
             "lbm_load": (ctypes.c_int, [_vp, ctypes.c_char_p]),
             "lbm_autotune": (ctypes.c_int, [_vp, ctypes.c_int]),
             "lbm_profile_steps": (ctypes.c_int, [_vp, ctypes.c_int64, _dp, _P(ctypes.c_int64)]),
+            "lbm_checks_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                  ctypes.c_int32, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp]),
             "lbm_last_error": (ctypes.c_char_p, [_vp]),
             "lbm_destroy": (None, [_vp]),
         }
@@ -274,3 +278,16 @@ class Context:
 
     def autotune(self, trial_steps=20):
         self._ck(self.L.lbm_autotune(self.h, int(trial_steps)))
+
+
+def checks_noalloc(d_populations, store, nx, ny, pitch, rho0, store_scale, d_solid, d_out3, stream=None):
+    """lbm_checks_noalloc on caller-owned device buffers (pointers or tensors); returns the status code."""
+    def ptr(t):
+        if t is None:
+            return None
+        return ctypes.c_void_p(t.data_ptr() if hasattr(t, "data_ptr") else int(t))
+    L = load()
+    st = STORES[store] if isinstance(store, str) else int(store)
+    return L.lbm_checks_noalloc(ptr(d_populations), st, int(nx), int(ny), int(pitch), float(rho0),
+                                float(store_scale), ptr(d_solid), ptr(d_out3),
+                                ctypes.c_void_p(stream) if stream else None)
