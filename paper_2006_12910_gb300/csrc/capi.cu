@@ -71,6 +71,15 @@ struct lbm_ctx {
     bool own_stream = false;
     cudaStream_t cap_stream = nullptr;
     cudaStream_t side = nullptr;
+    cudaStream_t far_stream = nullptr;   // branch running the far stream-collide items
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool overlap = true;                 // far items run concurrently with the particle kernels
+    int32_t* mark = nullptr;             // [2][total_items]
+    int32_t* near_list = nullptr;        // [2][total_items]
+    int32_t* near_cnt = nullptr;         // [2]
+    int64_t near_grid = 1;
+    LjEntry* lj_tab = nullptr;           // [ndom][LJ_TAB]
+    int32_t* lj_cnt = nullptr;           // [ndom]
     cudaEvent_t ev_snap = nullptr, ev_copied = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     bool graph_dirty = true;
@@ -131,6 +140,7 @@ int validate(const lbm_params& p, int d, lbm_ctx* c) {
     }
     if (p.max_particles < 0 || p.max_particles > 4096) return bad("max_particles must be in [0, 4096]");
     if (!(p.lj_psi >= 0.0) || !(p.lj_rit >= 0.0)) return bad("lj_psi and lj_rit must be >= 0");
+    if (p.lj_psi > 0.0 && !(p.lj_rit < 6.0)) return bad("lj_rit must be < 6 (offset table size)");
     return LBM_OK;
 }
 
@@ -242,6 +252,12 @@ void set_launch(lbm_ctx* c) {
     } else {
         c->grid = full;
     }
+    {
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        c->near_grid = std::min<int64_t>(full, 2 * (int64_t)sms);
+    }
     c->graph_dirty = true;
 }
 
@@ -260,10 +276,18 @@ PartArgs part_args(lbm_ctx* c, int cur) {
     a.nflips = c->nflips;
     a.diag = c->diag;
     a.err = c->err;
+    a.ctr = c->ctr + cur;
+    a.mark = c->mark;
+    a.near_list = c->near_list;
+    a.near_cnt = c->near_cnt;
+    a.total_items = c->total_items;
+    a.lj_tab = c->lj_tab;
+    a.lj_cnt = c->lj_cnt;
     return a;
 }
 
-cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int block, int64_t grid) {
+cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int block, int64_t grid,
+                                   int mode = STREAM_ALL) {
     StreamArgs a;
     a.doms = c->dd;
     a.item_off = c->d_item_off;
@@ -277,18 +301,33 @@ cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int bloc
     a.ctr_in = c->ctr + cur;
     a.ctr_out = c->ctr + (cur ^ 1);
     a.err = c->err;
+    a.mode = mode;
+    a.mark = c->mark;
+    a.near_list = c->near_list;
+    a.near_cnt = c->near_cnt;
     return launch_stream_collide(c->kind, c->noise, c->pl, a, block, grid, s);
 }
 
+// One timestep.  With particles the stream-collide items away from every
+// particle run on a second branch while the particle kernels and then the
+// near items run on the main branch; both branches join before the next step.
 cudaError_t enqueue_step(lbm_ctx* c, int cur, cudaStream_t s) {
-    if (c->np_active > 0) {
-        const PartArgs a = part_args(c, cur);
-        cudaError_t e = launch_particle_forces(c->kind, a, s);
-        if (e != cudaSuccess) return e;
-        e = launch_particle_links(c->kind, a, true, true, s);
-        if (e != cudaSuccess) return e;
+    if (c->np_active == 0) return enqueue_stream_collide(c, cur, s, c->block, c->grid, STREAM_ALL);
+    const PartArgs a = part_args(c, cur);
+    cudaError_t e;
+    if (!c->overlap) {
+        if ((e = launch_particle_forces(c->kind, a, s)) != cudaSuccess) return e;
+        if ((e = launch_particle_links(c->kind, a, PL_SWAP | PL_ADVANCE | PL_RASTER | PL_MARK, s)) != cudaSuccess) return e;
+        return enqueue_stream_collide(c, cur, s, c->block, c->grid, STREAM_ALL);
     }
-    return enqueue_stream_collide(c, cur, s, c->block, c->grid);
+    if ((e = cudaEventRecord(c->ev_fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c->far_stream, c->ev_fork, 0)) != cudaSuccess) return e;
+    if ((e = enqueue_stream_collide(c, cur, c->far_stream, c->block, c->grid, STREAM_FAR)) != cudaSuccess) return e;
+    if ((e = launch_particle_forces(c->kind, a, s)) != cudaSuccess) return e;
+    if ((e = launch_particle_links(c->kind, a, PL_SWAP | PL_ADVANCE | PL_RASTER | PL_MARK, s)) != cudaSuccess) return e;
+    if ((e = enqueue_stream_collide(c, cur, s, c->block, c->near_grid, STREAM_NEAR)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(c->ev_join, c->far_stream)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(s, c->ev_join, 0);
 }
 
 int build_graphs(lbm_ctx* c) {
@@ -301,7 +340,7 @@ int build_graphs(lbm_ctx* c) {
         cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
         if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); CKC(c, e); }
         CKC(c, e2);
-        e = cudaGraphInstantiate(&c->gexec[k], g, 0);
+        e = cudaGraphInstantiate(&c->gexec[k], g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         CKC(c, e);
     }
@@ -433,8 +472,47 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
         CKCR(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         c->own_stream = true;
     }
-    CKCR(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    {
+        int lo = 0, hi = 0;
+        CKCR(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        // the particle chain is the critical path of an overlapped step: highest priority
+        CKCR(cudaStreamCreateWithPriority(&c->cap_stream, cudaStreamNonBlocking, hi));
+        CKCR(cudaStreamCreateWithPriority(&c->far_stream, cudaStreamNonBlocking, lo));
+    }
     CKCR(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CKCR(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CKCR(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    CKCR(cudaMalloc(&c->mark, sizeof(int32_t) * 2 * std::max<int64_t>(1, c->total_items)));
+    CKCR(cudaMalloc(&c->near_list, sizeof(int32_t) * 2 * std::max<int64_t>(1, c->total_items)));
+    CKCR(cudaMalloc(&c->near_cnt, sizeof(int32_t) * 2));
+    CKCR(cudaMemsetAsync(c->mark, 0xff, sizeof(int32_t) * 2 * std::max<int64_t>(1, c->total_items), c->stream));
+    CKCR(cudaMemsetAsync(c->near_cnt, 0, sizeof(int32_t) * 2, c->stream));
+    {
+        // Eq. MP2 pair force per node offset within r_it, one table per domain
+        std::vector<LjEntry> tab((size_t)ndom * LJ_TAB);
+        std::vector<int32_t> cnt(ndom, 0);
+        for (int d = 0; d < ndom; ++d) {
+            const lbm_params& P = per_domain[d];
+            if (!(P.lj_psi > 0.0) || !(P.lj_rit > 0.0)) continue;
+            const int reach = (int)std::floor(P.lj_rit);
+            int m = 0;
+            for (int oy = -reach; oy <= reach; ++oy)
+                for (int ox = -reach; ox <= reach; ++ox) {
+                    if (ox == 0 && oy == 0) continue;
+                    const double dist = std::sqrt((double)(ox * ox + oy * oy));
+                    if (!(dist <= P.lj_rit) || m >= LJ_TAB) continue;
+                    const double mag = P.lj_psi * std::pow(dist / P.lj_rit, -13.0);
+                    tab[(size_t)d * LJ_TAB + m] = LjEntry{ox, oy, -mag * ox / dist, -mag * oy / dist};
+                    ++m;
+                }
+            cnt[d] = m;
+        }
+        CKCR(cudaMalloc(&c->lj_tab, sizeof(LjEntry) * tab.size()));
+        CKCR(cudaMalloc(&c->lj_cnt, sizeof(int32_t) * ndom));
+        CKCR(cudaMemcpyAsync(c->lj_tab, tab.data(), sizeof(LjEntry) * tab.size(), cudaMemcpyHostToDevice, c->stream));
+        CKCR(cudaMemcpyAsync(c->lj_cnt, cnt.data(), sizeof(int32_t) * ndom, cudaMemcpyHostToDevice, c->stream));
+        CKCR(cudaStreamSynchronize(c->stream));
+    }
     CKCR(cudaEventCreateWithFlags(&c->ev_snap, cudaEventDisableTiming));
     CKCR(cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming));
     CKCR(cudaMalloc(&c->f[0], c->arena_elems * c->esz));
@@ -483,6 +561,10 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->d_partial); cudaFree(c->d_sums); cudaFree(c->d_stage); cudaFree(c->d_mom);
     if (c->h_mom) cudaFreeHost(c->h_mom);
     free_particles(c);
+    cudaFree(c->mark); cudaFree(c->near_list); cudaFree(c->near_cnt); cudaFree(c->lj_tab); cudaFree(c->lj_cnt);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->far_stream) cudaStreamDestroy(c->far_stream);
     if (c->ev_snap) cudaEventDestroy(c->ev_snap);
     if (c->ev_copied) cudaEventDestroy(c->ev_copied);
     if (c->side) cudaStreamDestroy(c->side);
@@ -539,6 +621,9 @@ int lbm_add_particles(lbm_ctx* c, int dom, int n, const lbm_particle* p) {
         st.rho_p = q.rho_p;
         st.m = q.rho_p * pi * q.R * q.R;
         st.I = 0.5 * st.m * q.R * q.R;
+        st.inv_m = 1.0 / st.m;
+        st.inv_I = 1.0 / st.I;
+        st.buoy = (q.rho_p - P.rho0) / q.rho_p;
         st.dom = dom;
         st.fixed = q.fixed ? 1 : 0;
         const int r_up = (int)std::ceil(q.R);
@@ -577,8 +662,11 @@ int lbm_add_particles(lbm_ctx* c, int dom, int n, const lbm_particle* p) {
     CKC(c, cudaMemcpy(c->dd + dom, &D, sizeof(DomDev), cudaMemcpyHostToDevice));
     c->links_total = lo;
     c->flips_total = fo;
-    // rasterise every particle at its current position (no link exchange, no flips)
-    CKC(c, launch_particle_links(c->kind, part_args(c, c->cur), false, false, c->stream));
+    // rasterise every particle at its current position (no link exchange, no
+    // flips) and mark the work items near the particles for the next step
+    CKC(c, cudaMemsetAsync(c->mark, 0xff, sizeof(int32_t) * 2 * std::max<int64_t>(1, c->total_items), c->stream));
+    CKC(c, cudaMemsetAsync(c->near_cnt, 0, sizeof(int32_t) * 2, c->stream));
+    CKC(c, launch_particle_links(c->kind, part_args(c, c->cur), PL_RASTER | PL_MARK, c->stream));
     c->graph_dirty = true;
     return sync_and_check(c);
 }
@@ -871,7 +959,12 @@ int lbm_load(lbm_ctx* c, const char* path) {
         for (int d = 0; d < c->ndom; ++d) c->hd[d].np = dnp[d];
         c->np_active = np_total;
         CKC(c, cudaMemcpy(c->dd, c->hd.data(), sizeof(DomDev) * c->ndom, cudaMemcpyHostToDevice));
+        CKC(c, cudaMemset(c->mark, 0xff, sizeof(int32_t) * 2 * std::max<int64_t>(1, c->total_items)));
+        CKC(c, cudaMemset(c->near_cnt, 0, sizeof(int32_t) * 2));
+        CKC(c, launch_particle_links(c->kind, part_args(c, c->cur), PL_MARK, c->stream));
+        CKC(c, cudaStreamSynchronize(c->stream));
     }
+    CKC(c, cudaMemcpy(c->dd, c->hd.data(), sizeof(DomDev) * c->ndom, cudaMemcpyHostToDevice));
     c->steps = h.steps;
     c->graph_dirty = true;
     return LBM_OK;
@@ -893,7 +986,7 @@ int lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double* ms_out3, int64_t* laun
             CKC(c, cudaEventRecord(ev[0], c->stream));
             CKC(c, launch_particle_forces(c->kind, a, c->stream));
             CKC(c, cudaEventRecord(ev[1], c->stream));
-            CKC(c, launch_particle_links(c->kind, a, true, true, c->stream));
+            CKC(c, launch_particle_links(c->kind, a, PL_SWAP | PL_ADVANCE | PL_RASTER | PL_MARK, c->stream));
             CKC(c, cudaEventRecord(ev[2], c->stream));
             launches += 2;
         }

@@ -117,20 +117,32 @@ __device__ __forceinline__ double full_pop(const typename S::T* base, const DomD
     return S::SHIFT ? v + wgt(i) * D.rho0 : v;
 }
 
-// Fixed-order block reduction of N doubles (deterministic for a fixed blockDim).
+// Fixed-order block reduction of N doubles (deterministic for a fixed
+// blockDim).  Shuffle trees inside each warp with the N components
+// interleaved (FP64 latency is long on this part, so the adds of one level
+// are issued together), then lane c of warp 0 adds the per-warp results of
+// component c as a balanced tree.  The totals land in tot[0..N).
 template <int N>
-__device__ __forceinline__ void block_sum(double (&v)[N], double (*sh)[PBLOCK]) {
+__device__ __forceinline__ void block_sum(double (&v)[N], double (*sh)[PBLOCK / 32], double* tot) {
+    static_assert(PBLOCK == 256, "the cross-warp tree below assumes 8 warps");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int c = 0; c < N; ++c) sh[c][threadIdx.x] = v[c];
-    __syncthreads();
-    for (int s = PBLOCK / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s)
+    for (int o = 16; o > 0; o >>= 1) {
+        double t[N];
 #pragma unroll
-            for (int c = 0; c < N; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + s];
-        __syncthreads();
+        for (int c = 0; c < N; ++c) t[c] = __shfl_down_sync(0xffffffffu, v[c], o);
+#pragma unroll
+        for (int c = 0; c < N; ++c) v[c] += t[c];
     }
+    if (lane == 0) {
 #pragma unroll
-    for (int c = 0; c < N; ++c) v[c] = sh[c][0];
+        for (int c = 0; c < N; ++c) sh[c][w] = v[c];
+    }
+    __syncthreads();
+    if (w == 0 && lane < N) {
+        const double* r = sh[lane];
+        tot[lane] = ((r[0] + r[1]) + (r[2] + r[3])) + ((r[4] + r[5]) + (r[6] + r[7]));
+    }
     __syncthreads();
 }
 
@@ -156,7 +168,6 @@ __device__ __forceinline__ int block_scan(int c, int* sh_warp, int& excl) {
 }
 
 constexpr int PB_CAP = 4096;   // nodes of a shared-memory inside bitmap
-constexpr int LJ_MAXOFF = 128;  // offsets within the LJ threshold held in shared memory
 constexpr int MAXNEAR = 64;     // nearby particles considered per particle
 
 // Exclusive block scan of small non-negative counts; returns the block total.
@@ -179,9 +190,12 @@ __device__ __forceinline__ void near_list(const PartArgs& a, const DomDev& D, in
         if (j < D.np && p2 != p) {
             o = states[p2];
             r2 = a.st[p2].R;
-            const double dx = min_image(o.x - x, D.nx, D.flags & FLAG_PX);
-            const double dy = min_image(o.y - y, D.ny, D.flags & FLAG_PY);
-            const double reach = R + r2 + extra;
+            // FP32 centre distance with a one-node margin: a superset of the
+            // particles within reach is all that is needed here
+            float dx = (float)o.x - (float)x, dy = (float)o.y - (float)y;
+            if (D.flags & FLAG_PX) { const float L = (float)D.nx; dx -= L * rintf(dx / L); }
+            if (D.flags & FLAG_PY) { const float L = (float)D.ny; dy -= L * rintf(dy / L); }
+            const float reach = (float)(R + r2 + extra) + 1.0f;
             hit = dx * dx + dy * dy <= reach * reach;
         }
         int excl;
@@ -209,20 +223,24 @@ __device__ __forceinline__ bool is_surface_f(const DomDev& D, const DiskF& k, in
 template <class S>
 __global__ void __launch_bounds__(PBLOCK) k_particle_forces(PartArgs a) {
     const int p = blockIdx.x;
+    // The link kernel that follows appends the items near each particle for
+    // step t+1; empty that list first (its last reader finished a step ago).
+    if (p == 0 && threadIdx.x == 0 && a.near_cnt) a.near_cnt[(*a.ctr + 1) & 1] = 0;
     const PartStatic st = a.st[p];
     if (st.dom < 0) return;
-    const DomDev& D = a.doms[st.dom];
+    const DomDev D = a.doms[st.dom];
     if (p - D.p0 >= D.np) return;
     const PartState q = a.cur[p];
     const typename S::T* base = static_cast<const typename S::T*>(a.arena) + D.off;
     const bool px = D.flags & FLAG_PX, py = D.flags & FLAG_PY;
-    __shared__ double sh[DIAG_N][PBLOCK];
+    __shared__ double sh[DIAG_N][PBLOCK / 32];
+    __shared__ double tot[DIAG_N];
     __shared__ uint8_t bm[PB_CAP];
-    __shared__ double lj_fx[LJ_MAXOFF], lj_fy[LJ_MAXOFF];
-    __shared__ int lj_ox[LJ_MAXOFF], lj_oy[LJ_MAXOFF];
-    __shared__ uint8_t lj_ok[LJ_MAXOFF];
+    __shared__ double lj_fx[LJ_TAB], lj_fy[LJ_TAB];
+    __shared__ int lj_ox[LJ_TAB], lj_oy[LJ_TAB];
     __shared__ int lj_n, nnear;
     __shared__ int sh_warp[PBLOCK / 32];
+    __shared__ uint8_t wall_win[PB_CAP];
     __shared__ int near[MAXNEAR];
     __shared__ DiskF near_d[MAXNEAR];
 
@@ -286,32 +304,33 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_forces(PartArgs a) {
         const Box e = {b.x0 - 1, b.y0 - 1, b.w + 2, b.h + 2};
         const int reach = (int)floor(D.lj_rit);
         const bool use_bm = e.n() <= PB_CAP;
-        // Offset table of the pair force within r_it: entry t holds offset
-        // (t % w - reach, t / w - reach) and psi (d/r_it)^-13 (-o)/d, or zero.
-        const int ow = 2 * reach + 1;
-        if (threadIdx.x == 0) lj_n = ow * ow <= LJ_MAXOFF ? ow * ow : LJ_MAXOFF;
-        for (int t = threadIdx.x; t < ow * ow && t < LJ_MAXOFF; t += PBLOCK) {
-            const int ox = t % ow - reach, oy = t / ow - reach;
-            const double dist = sqrt((double)(ox * ox + oy * oy));
-            lj_ox[t] = ox;
-            lj_oy[t] = oy;
-            if ((ox == 0 && oy == 0) || !(dist <= D.lj_rit)) {
-                lj_ok[t] = 0;
-                lj_fx[t] = 0.0;
-                lj_fy[t] = 0.0;
-            } else {
-                const double x1 = dist / D.lj_rit, x2 = x1 * x1, x4 = x2 * x2, x8 = x4 * x4;
-                const double mag = D.lj_psi / (x8 * x4 * x1);
-                lj_ok[t] = 1;
-                lj_fx[t] = -mag * ox / dist;
-                lj_fy[t] = -mag * oy / dist;
-            }
+        // Offset table of Eq. MP2 (built once on the host for this domain).
+        if (threadIdx.x == 0) lj_n = a.lj_cnt[st.dom];
+        for (int t = threadIdx.x; t < LJ_TAB; t += PBLOCK) {
+            const LjEntry en = a.lj_tab[(int64_t)st.dom * LJ_TAB + t];
+            lj_ox[t] = en.ox;
+            lj_oy[t] = en.oy;
+            lj_fx[t] = en.fx;
+            lj_fy[t] = en.fy;
         }
         near_list(a, D, p, a.cur, q.x, q.y, R, D.lj_rit + 4.0, near, near_d, &nnear, sh_warp);
         if (use_bm) {
             const DiskF kf = make_diskf(q.x, q.y, R);
             for (int t = threadIdx.x; t < e.n(); t += PBLOCK)
                 bm[t] = inside_f(D, kf, e.x0 + t % e.w, e.y0 + t / e.w, false) ? 1 : 0;
+        }
+        // Solid / wall status of every node within r_it of the box, staged once:
+        // 1 = wall or solid node, 0 = fluid or outside an open end.
+        const Box W = {b.x0 - reach, b.y0 - reach, b.w + 2 * reach, b.h + 2 * reach};
+        const bool use_win = W.n() <= PB_CAP;
+        if (use_win) {
+            for (int t = threadIdx.x; t < W.n(); t += PBLOCK) {
+                int wx = W.x0 + t % W.w, wy = W.y0 + t / W.w;
+                uint8_t v = 0;
+                if ((D.flags & FLAG_WY) && (wy < 0 || wy >= D.ny)) v = 1;
+                else if (wrap_node(D, wx, wy)) v = a.solid[D.node_off + (int64_t)wy * D.pitch + wx] != 0;
+                wall_win[t] = v;
+            }
         }
         __syncthreads();
         const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
@@ -331,7 +350,8 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_forces(PartArgs a) {
                 surf = is_surface(D, q.x, q.y, R, ax, ay);
             }
             if (!surf) continue;
-            const double rax = min_image(ax - q.x, D.nx, px), ray = min_image(ay - q.y, D.ny, py);
+            double rax = 0.0, ray = 0.0;
+            bool arm = false;  // torque arm of this surface node, computed on first use
             for (int j = 0; j < nn; ++j) {
                 const DiskF& ko = near_d[j];
                 // only surface nodes of p within r_it of the other disk's rim can pair
@@ -340,27 +360,31 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_forces(PartArgs a) {
                 const float lim = (float)(ko.R + D.lj_rit) + 2.0f;
                 if (ddx * ddx + ddy * ddy > lim * lim) continue;
                 for (int w = 0; w < lj_n; ++w) {
-                    if (!lj_ok[w]) continue;
                     // node b = a + o expressed in the other particle's own frame
                     const int bx = ko.cx + wrap_off(ax + lj_ox[w] - ko.cx, D.nx, px);
                     const int by = ko.cy + wrap_off(ay + lj_oy[w] - ko.cy, D.ny, py);
                     if (!is_surface_f(D, ko, bx, by)) continue;
-                    // repulsion on a from b = a + o: psi (d/r_it)^-13 (a - b)/d, the table entry of o
+                    // repulsion on a from b = a + o, the table entry of o
+                    if (!arm) { rax = min_image(ax - q.x, D.nx, px); ray = min_image(ay - q.y, D.ny, py); arm = true; }
                     acc[6] += lj_fx[w];
                     acc[7] += lj_fy[w];
                     acc[8] += rax * lj_fy[w] - ray * lj_fx[w];
                 }
             }
+#pragma unroll 1
             for (int j = 0; j < lj_n; ++j) {
-                if (!lj_ok[j]) continue;
                 int wx = ax + lj_ox[j], wy = ay + lj_oy[j];
                 bool wall;
-                if ((D.flags & FLAG_WY) && (wy < 0 || wy >= D.ny)) wall = true;
-                else {
+                if (use_win) {
+                    wall = wall_win[(wy - W.y0) * W.w + (wx - W.x0)] != 0;
+                } else if ((D.flags & FLAG_WY) && (wy < 0 || wy >= D.ny)) {
+                    wall = true;
+                } else {
                     if (!wrap_node(D, wx, wy)) continue;
                     wall = a.solid[D.node_off + (int64_t)wy * D.pitch + wx] != 0;
                 }
                 if (!wall) continue;
+                if (!arm) { rax = min_image(ax - q.x, D.nx, px); ray = min_image(ay - q.y, D.ny, py); arm = true; }
                 acc[6] += lj_fx[j];
                 acc[7] += lj_fy[j];
                 acc[8] += rax * lj_fy[j] - ray * lj_fx[j];
@@ -368,19 +392,17 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_forces(PartArgs a) {
         }
     }
 
-    block_sum<DIAG_N>(acc, sh);
+    block_sum<DIAG_N>(acc, sh, tot);
+    if (threadIdx.x < DIAG_N) a.diag[(int64_t)p * DIAG_N + threadIdx.x] = tot[threadIdx.x];
     if (threadIdx.x == 0) {
-        double* dg = a.diag + (int64_t)p * DIAG_N;
-        for (int c = 0; c < DIAG_N; ++c) dg[c] = acc[c];
         // Eqs. MP5, MP6; r_c(t+1) = r_c(t) + U_p(t).
         PartState n = q;
         if (!st.fixed) {
-            const double Fx = acc[0] + acc[3] + acc[6], Fy = acc[1] + acc[4] + acc[7];
-            const double T = acc[2] + acc[5] + acc[8];
-            const double buoy = (st.rho_p - D.rho0) / st.rho_p;
-            n.U = q.U + Fx / st.m + buoy * D.gx;
-            n.V = q.V + Fy / st.m + buoy * D.gy;
-            n.Om = q.Om + T / st.I;
+            const double Fx = (tot[0] + tot[3]) + tot[6], Fy = (tot[1] + tot[4]) + tot[7];
+            const double T = (tot[2] + tot[5]) + tot[8];
+            n.U = q.U + Fx * st.inv_m + st.buoy * D.gx;
+            n.V = q.V + Fy * st.inv_m + st.buoy * D.gy;
+            n.Om = q.Om + T * st.inv_I;
             n.x = q.x + q.U;
             n.y = q.y + q.V;
             n.th = q.th + q.Om;
@@ -392,18 +414,19 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_forces(PartArgs a) {
 }
 
 template <class S>
-__global__ void __launch_bounds__(PBLOCK) k_particle_links(PartArgs a, int swap, int advance) {
+__global__ void __launch_bounds__(PBLOCK) k_particle_links(PartArgs a, int modes) {
+    const bool swap = modes & PL_SWAP, advance = modes & PL_ADVANCE;
     typedef typename S::A A;
     const int p = blockIdx.x;
     const PartStatic st = a.st[p];
     if (st.dom < 0) return;
-    const DomDev& D = a.doms[st.dom];
+    const DomDev D = a.doms[st.dom];
     if (p - D.p0 >= D.np) return;
     const PartState q = a.cur[p];
     typename S::T* base = static_cast<typename S::T*>(a.arena) + D.off;
     const bool px = D.flags & FLAG_PX, py = D.flags & FLAG_PY;
     __shared__ int sh_warp[PBLOCK / 32];
-    __shared__ uint8_t bnew[PB_CAP], bold[PB_CAP];
+    __shared__ uint8_t bnew[PB_CAP], bold[PB_CAP], node_st[PB_CAP];
     __shared__ int near[MAXNEAR];
     __shared__ DiskF near_d[MAXNEAR];
     __shared__ int nnear;
@@ -434,6 +457,37 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_links(PartArgs a, int swap,
     const PartState n = advance ? a.next[p] : q;
     const PartState* others = advance ? a.next : a.cur;
     const double R = st.R;
+    if (modes & PL_MARK) {
+        // Work items (row segments) within two nodes of the disk's box at the
+        // step the state is about to reach are "near": the stream-collide pass
+        // of that step runs them only after this particle's link exchange.
+        const int64_t t_mark = advance ? *a.ctr + 1 : *a.ctr;
+        const int par = (int)(t_mark & 1);
+        const Box bm2 = disk_box(n.x, n.y, R);
+        const int seg_w = 32 * D.V;
+        const int xs = bm2.x0 - 2, xe = bm2.x0 + bm2.w + 1;
+        for (int r = threadIdx.x; r < bm2.h + 4; r += PBLOCK) {
+            int y = bm2.y0 - 2 + r, xdummy = 0;
+            if (!wrap_node(D, xdummy, y)) continue;
+            for (int xx = xs;; xx += seg_w) {
+                const int xc = xx < xe ? xx : xe;
+                int x = xc, yd = 0;
+                if (wrap_node(D, x, yd)) {
+                    const int64_t item = D.item_off + (int64_t)y * D.seg_per_row + x / seg_w;
+                    int32_t* m = a.mark + (int64_t)par * a.total_items + item;
+                    if (atomicExch(m, (int32_t)t_mark) != (int32_t)t_mark) {
+                        const int slot = atomicAdd(a.near_cnt + par, 1);
+                        a.near_list[(int64_t)par * a.total_items + slot] = (int32_t)item;
+                    }
+                }
+                if (xc == xe) break;
+            }
+        }
+    }
+    if (!(modes & PL_RASTER)) {
+        if (advance && threadIdx.x == 0) a.cur[p] = n;
+        return;
+    }
     // Union of the old and new boxes; every neighbour of a node inside either
     // disk lies in it.
     const Box bo = disk_box(q.x, q.y, R), bn = disk_box(n.x, n.y, R);
@@ -452,6 +506,9 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_links(PartArgs a, int swap,
             const int xu = U.x0 + t % U.w, yu = U.y0 + t / U.w;
             bnew[t] = inside_f(D, kn, xu, yu, true) ? 1 : 0;
             bold[t] = advance ? (inside_f(D, ko, xu, yu, true) ? 1 : 0) : bnew[t];
+            // 0 = fluid node in the domain, 1 = solid, 2 = outside an open end
+            int x = xu, y = yu;
+            node_st[t] = wrap_node(D, x, y) ? (a.solid[D.node_off + (int64_t)y * D.pitch + x] ? 1 : 0) : 2;
         }
     }
     __syncthreads();
@@ -480,7 +537,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_links(PartArgs a, int swap,
             int x = xu, y = yu;
             if (wrap_node(D, x, y)) {
                 node = y * D.pitch + x;
-                const bool solid_here = a.solid[D.node_off + node] != 0;
+                const bool solid_here = use_bm ? node_st[t] == 1 : a.solid[D.node_off + node] != 0;
                 const bool now = in_new(xu, yu);
                 if (now) {
                     for (int j = 0; j < nn; ++j)
@@ -490,8 +547,12 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_links(PartArgs a, int swap,
                         for (int k = 1; k < 9; ++k) {
                             const int fxu = xu + cx(k), fyu = yu + cy(k);
                             int fx = fxu, fy = fyu;
-                            if (!wrap_node(D, fx, fy)) continue;
-                            if (a.solid[D.node_off + (int64_t)fy * D.pitch + fx]) continue;
+                            if (use_bm) {
+                                if (node_st[(fyu - U.y0) * U.w + (fxu - U.x0)] != 0) continue;
+                            } else {
+                                if (!wrap_node(D, fx, fy)) continue;
+                                if (a.solid[D.node_off + (int64_t)fy * D.pitch + fx]) continue;
+                            }
                             bool in_any = in_new(fxu, fyu);
                             for (int j = 0; j < nn && !in_any; ++j) in_any = inside_f(D, near_d[j], fxu, fyu, true);
                             if (!in_any) mask |= 1u << k;
@@ -543,9 +604,9 @@ cudaError_t launch_particle_forces(int kind, const PartArgs& a, cudaStream_t s) 
     return cudaGetLastError();
 }
 
-cudaError_t launch_particle_links(int kind, const PartArgs& a, bool swap, bool advance, cudaStream_t s) {
+cudaError_t launch_particle_links(int kind, const PartArgs& a, int modes, cudaStream_t s) {
     if (a.np <= 0) return cudaSuccess;
-    LBM_PDISPATCH(kind, (k_particle_links<S><<<a.np, PBLOCK, 0, s>>>(a, swap ? 1 : 0, advance ? 1 : 0)));
+    LBM_PDISPATCH(kind, (k_particle_links<S><<<a.np, PBLOCK, 0, s>>>(a, modes)));
     return cudaGetLastError();
 }
 

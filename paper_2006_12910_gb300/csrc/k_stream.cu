@@ -97,13 +97,18 @@ __global__ void __launch_bounds__(512) k_stream_collide(StreamArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t step64 = *a.ctr_in;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.ctr_out = step64 + 1;
+    if (a.mode != STREAM_NEAR && blockIdx.x == 0 && threadIdx.x == 0) *a.ctr_out = step64 + 1;
     const uint32_t step = (uint32_t)step64;
+    const int par = (int)(step64 & 1);
     const T* __restrict__ src = static_cast<const T*>(a.src);
     T* __restrict__ dst = static_cast<T*>(a.dst);
     bool ok = true;
+    const int64_t count = a.mode == STREAM_NEAR ? (int64_t)__ldg(a.near_cnt + par) : a.total_items;
 
-    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < a.total_items; g += nwarps) {
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < count; w += nwarps) {
+        int64_t g = w;
+        if (a.mode == STREAM_NEAR) g = __ldg(a.near_list + (int64_t)par * a.total_items + w);
+        else if (a.mode == STREAM_FAR && __ldg(a.mark + (int64_t)par * a.total_items + w) == (int32_t)step64) continue;
         const int d = a.ndom == 1 ? 0 : find_domain(a.item_off, a.ndom, g);
         const DomDev& D = a.doms[d];
         const int nx = D.nx, ny = D.ny, flags = D.flags;

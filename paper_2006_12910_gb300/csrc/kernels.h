@@ -21,7 +21,15 @@ struct StreamArgs {
     const int64_t* ctr_in;    // step counter of the source state
     int64_t* ctr_out;         // step counter of the destination state
     unsigned* err;            // sticky device error bits
+    // Work selection: STREAM_ALL every item; STREAM_FAR the items not marked
+    // near a particle for this step (mark[step & 1][item] != step);
+    // STREAM_NEAR the items in near_list[step & 1][0 .. near_cnt[step & 1]).
+    int mode;
+    const int32_t* mark;      // [2][total_items]
+    const int32_t* near_list; // [2][total_items]
+    const int32_t* near_cnt;  // [2]
 };
+enum { STREAM_ALL = 0, STREAM_FAR = 1, STREAM_NEAR = 2 };
 
 cudaError_t launch_stream_collide(int kind, bool noise, bool pl, const StreamArgs& a, int block, int64_t grid,
                                   cudaStream_t s);
@@ -60,8 +68,19 @@ struct PartArgs {
     int32_t* nflips;
     double* diag;              // np * DIAG_N
     unsigned* err;
+    // near-item bookkeeping for the overlapped step (see StreamArgs)
+    const int64_t* ctr;        // step counter of the state in `arena`
+    int32_t* mark;             // [2][total_items]
+    int32_t* near_list;        // [2][total_items]
+    int32_t* near_cnt;         // [2]
+    int64_t total_items;
+    const LjEntry* lj_tab;     // [ndom][LJ_TAB], valid entries first
+    const int32_t* lj_cnt;     // [ndom]
 };
+// Link-kernel modes: exchange the link slots, advance the state, rebuild the
+// link / flip lists, mark the work items near each particle for the next step.
+enum { PL_SWAP = 1, PL_ADVANCE = 2, PL_RASTER = 4, PL_MARK = 8 };
 cudaError_t launch_particle_forces(int kind, const PartArgs& a, cudaStream_t s);
-cudaError_t launch_particle_links(int kind, const PartArgs& a, bool swap, bool advance, cudaStream_t s);
+cudaError_t launch_particle_links(int kind, const PartArgs& a, int modes, cudaStream_t s);
 
 }  // namespace lbmk

@@ -58,9 +58,18 @@ struct PartState {
 };
 struct PartStatic {
     double R, rho_p, m, I;
+    double inv_m, inv_I, buoy;  // 1/m_p, 1/I_p and (rho_p - rho0)/rho_p (Eq. MP5)
     int32_t dom, fixed;
     int32_t link_cap, flip_cap;
     int64_t link_off, flip_off;
+};
+
+// Pair force of Eq. MP2 for one node offset o within the threshold r_it:
+// psi (|o|/r_it)^-13 (-o)/|o|, the force on a node from a node at +o.
+constexpr int LJ_TAB = 128;
+struct LjEntry {
+    int32_t ox, oy;
+    double fx, fy;
 };
 
 constexpr int DIAG_N = 13;  // F_links(2), T_links, F_cu(2), T_cu, F_lj(2), T_lj, n_cov, n_unc, m_cov, m_unc
