@@ -222,7 +222,7 @@ def main():
     ctx = make_ctx(args.store)
     if not args.no_autotune:
         ctx.autotune(20)
-    kernels_per_step = 3 if w.particles else 1
+    kernels_per_step = 3 if w.particles else 1  # far stream-collide, particle step, near stream-collide
 
     def barrier():
         if world > 1:
@@ -268,7 +268,8 @@ def main():
                 "traffic": None, "kernel": "k_stream_collide", "peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "kernel_ms": k1_ms,
                 "kernel_share": kk / max(kf + kl + kk, 1e-9),
-                "particle_kernels_ms": [kf / args.profile_steps, kl / args.profile_steps]}
+                "particle_kernel_ms": kf / args.profile_steps,
+                "step_overlap": "far stream-collide items run concurrently with the particle kernel"}
 
     # ---- end to end through the C ABI with host buffers ------------------------------------
     # Upload the initial state from pinned host memory, then every step: advance and read

@@ -176,12 +176,12 @@ int lbm_load(lbm_ctx* ctx, const char* path);
  * and restored around the trials. */
 int lbm_autotune(lbm_ctx* ctx, int trial_steps);
 
-/* Measurement: advance nsteps timesteps with plain launches (no graph) and a
- * CUDA-event pair around every kernel on the context stream; ms_out[0..2]
- * receive the summed device time of the particle-force kernel, the
- * link-exchange kernel and the stream-and-collide kernel, and launches_out
- * (if not NULL) the number of kernels launched.  Blocking.  The state
- * advances exactly as with lbm_step. */
+/* Measurement: advance nsteps timesteps with plain launches in sequence (no
+ * graph, no overlap) and a CUDA-event pair around every kernel on the
+ * context stream; ms_out[0] receives the summed device time of the particle
+ * kernel, ms_out[1] 0 (reserved), ms_out[2] that of the stream-and-collide
+ * kernel over every work item, and launches_out (if not NULL) the number of
+ * kernels launched.  Blocking.  The state advances exactly as with lbm_step. */
 int lbm_profile_steps(lbm_ctx* ctx, int64_t nsteps, double* ms_out3, int64_t* launches_out);
 
 /* Largest row count lbm_checks_noalloc accepts (its static scratch holds one

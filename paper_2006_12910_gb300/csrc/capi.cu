@@ -57,8 +57,7 @@ struct lbm_ctx {
     int np_active = 0;
     std::vector<PartStatic> hst;
     std::vector<PartState> hstate;  // host shadow used while adding
-    PartState* pcur = nullptr;
-    PartState* pnext = nullptr;
+    PartState* pstate = nullptr;          // [2][np_slots], slot (step & 1) is current
     PartStatic* pst = nullptr;
     int32_t* links = nullptr;
     int32_t* nlinks = nullptr;
@@ -75,8 +74,10 @@ struct lbm_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool overlap = true;                 // far items run concurrently with the particle kernels
     int32_t* mark = nullptr;             // [2][total_items]
-    int32_t* near_list = nullptr;        // [2][total_items]
-    int32_t* near_cnt = nullptr;         // [2]
+    int32_t* near_list = nullptr;        // [3][total_items]
+    int32_t* near_cnt = nullptr;         // [3]
+    int64_t* fliptag = nullptr;          // per node
+    double* flipmom = nullptr;           // [2][flips_total][3]
     int64_t near_grid = 1;
     LjEntry* lj_tab = nullptr;           // [ndom][LJ_TAB]
     int32_t* lj_cnt = nullptr;           // [ndom]
@@ -266,14 +267,17 @@ PartArgs part_args(lbm_ctx* c, int cur) {
     a.doms = c->dd;
     a.arena = c->f[cur];
     a.solid = c->solid;
-    a.cur = c->pcur;
-    a.next = c->pnext;
+    a.state = c->pstate;
+    a.flipmom = c->flipmom;
+    a.fliptag = c->fliptag;
     a.st = c->pst;
     a.np = c->np_slots;
     a.links = c->links;
     a.nlinks = c->nlinks;
     a.flips = c->flips;
     a.nflips = c->nflips;
+    a.links_total = c->links_total;
+    a.flips_total = c->flips_total;
     a.diag = c->diag;
     a.err = c->err;
     a.ctr = c->ctr + cur;
@@ -305,6 +309,8 @@ cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int bloc
     a.mark = c->mark;
     a.near_list = c->near_list;
     a.near_cnt = c->near_cnt;
+    a.fliptag = c->fliptag;
+    a.flipmom = c->flipmom;
     return launch_stream_collide(c->kind, c->noise, c->pl, a, block, grid, s);
 }
 
@@ -316,15 +322,13 @@ cudaError_t enqueue_step(lbm_ctx* c, int cur, cudaStream_t s) {
     const PartArgs a = part_args(c, cur);
     cudaError_t e;
     if (!c->overlap) {
-        if ((e = launch_particle_forces(c->kind, a, s)) != cudaSuccess) return e;
-        if ((e = launch_particle_links(c->kind, a, PL_SWAP | PL_ADVANCE | PL_RASTER | PL_MARK, s)) != cudaSuccess) return e;
+        if ((e = launch_particle_step(c->kind, a, PL_STEP, s)) != cudaSuccess) return e;
         return enqueue_stream_collide(c, cur, s, c->block, c->grid, STREAM_ALL);
     }
     if ((e = cudaEventRecord(c->ev_fork, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(c->far_stream, c->ev_fork, 0)) != cudaSuccess) return e;
     if ((e = enqueue_stream_collide(c, cur, c->far_stream, c->block, c->grid, STREAM_FAR)) != cudaSuccess) return e;
-    if ((e = launch_particle_forces(c->kind, a, s)) != cudaSuccess) return e;
-    if ((e = launch_particle_links(c->kind, a, PL_SWAP | PL_ADVANCE | PL_RASTER | PL_MARK, s)) != cudaSuccess) return e;
+    if ((e = launch_particle_step(c->kind, a, PL_STEP, s)) != cudaSuccess) return e;
     if ((e = enqueue_stream_collide(c, cur, s, c->block, c->near_grid, STREAM_NEAR)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(c->ev_join, c->far_stream)) != cudaSuccess) return e;
     return cudaStreamWaitEvent(s, c->ev_join, 0);
@@ -395,9 +399,9 @@ int check_dom(lbm_ctx* c, int dom) {
 }
 
 void free_particles(lbm_ctx* c) {
-    cudaFree(c->pcur); cudaFree(c->pnext); cudaFree(c->pst);
+    cudaFree(c->pstate); cudaFree(c->pst); cudaFree(c->flipmom);
     cudaFree(c->links); cudaFree(c->nlinks); cudaFree(c->flips); cudaFree(c->nflips); cudaFree(c->diag);
-    c->pcur = c->pnext = nullptr; c->pst = nullptr;
+    c->pstate = nullptr; c->pst = nullptr; c->flipmom = nullptr;
     c->links = c->nlinks = c->flips = c->nflips = nullptr;
     c->diag = nullptr;
 }
@@ -483,10 +487,12 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
     CKCR(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     CKCR(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     CKCR(cudaMalloc(&c->mark, sizeof(int32_t) * 2 * std::max<int64_t>(1, c->total_items)));
-    CKCR(cudaMalloc(&c->near_list, sizeof(int32_t) * 2 * std::max<int64_t>(1, c->total_items)));
-    CKCR(cudaMalloc(&c->near_cnt, sizeof(int32_t) * 2));
+    CKCR(cudaMalloc(&c->near_list, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items)));
+    CKCR(cudaMalloc(&c->near_cnt, sizeof(int32_t) * 3));
     CKCR(cudaMemsetAsync(c->mark, 0xff, sizeof(int32_t) * 2 * std::max<int64_t>(1, c->total_items), c->stream));
-    CKCR(cudaMemsetAsync(c->near_cnt, 0, sizeof(int32_t) * 2, c->stream));
+    CKCR(cudaMemsetAsync(c->near_cnt, 0, sizeof(int32_t) * 3, c->stream));
+    CKCR(cudaMalloc(&c->fliptag, sizeof(int64_t) * std::max<size_t>(1, c->node_bytes)));
+    CKCR(cudaMemsetAsync(c->fliptag, 0xff, sizeof(int64_t) * std::max<size_t>(1, c->node_bytes), c->stream));
     {
         // Eq. MP2 pair force per node offset within r_it, one table per domain
         std::vector<LjEntry> tab((size_t)ndom * LJ_TAB);
@@ -562,6 +568,7 @@ void lbm_destroy(lbm_ctx* c) {
     if (c->h_mom) cudaFreeHost(c->h_mom);
     free_particles(c);
     cudaFree(c->mark); cudaFree(c->near_list); cudaFree(c->near_cnt); cudaFree(c->lj_tab); cudaFree(c->lj_cnt);
+    cudaFree(c->fliptag);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->far_stream) cudaStreamDestroy(c->far_stream);
@@ -611,7 +618,8 @@ int lbm_add_particles(lbm_ctx* c, int dom, int n, const lbm_particle* p) {
     CKC(c, cudaStreamSynchronize(c->stream));
     // refresh the host shadow of the existing particle states
     if (c->np_active > 0)
-        CKC(c, cudaMemcpy(c->hstate.data(), c->pcur, sizeof(PartState) * c->np_slots, cudaMemcpyDeviceToHost));
+        CKC(c, cudaMemcpy(c->hstate.data(), c->pstate + (c->steps & 1) * c->np_slots, sizeof(PartState) * c->np_slots,
+                          cudaMemcpyDeviceToHost));
     const double pi = 3.14159265358979323846264338327950288;
     for (int i = 0; i < n; ++i) {
         const lbm_particle& q = p[i];
@@ -645,19 +653,19 @@ int lbm_add_particles(lbm_ctx* c, int dom, int n, const lbm_particle* p) {
     }
     free_particles(c);
     const size_t ns = c->np_slots;
-    CKC(c, cudaMalloc(&c->pcur, sizeof(PartState) * ns));
-    CKC(c, cudaMalloc(&c->pnext, sizeof(PartState) * ns));
+    CKC(c, cudaMalloc(&c->pstate, sizeof(PartState) * 2 * ns));
+    CKC(c, cudaMalloc(&c->flipmom, sizeof(double) * 2 * 3 * std::max<int64_t>(fo, 1)));
     CKC(c, cudaMalloc(&c->pst, sizeof(PartStatic) * ns));
-    CKC(c, cudaMalloc(&c->links, sizeof(int32_t) * std::max<int64_t>(lo, 1)));
-    CKC(c, cudaMalloc(&c->flips, sizeof(int32_t) * std::max<int64_t>(fo, 1)));
-    CKC(c, cudaMalloc(&c->nlinks, sizeof(int32_t) * ns));
-    CKC(c, cudaMalloc(&c->nflips, sizeof(int32_t) * ns));
+    CKC(c, cudaMalloc(&c->links, sizeof(int32_t) * 2 * std::max<int64_t>(lo, 1)));
+    CKC(c, cudaMalloc(&c->flips, sizeof(int32_t) * 2 * std::max<int64_t>(fo, 1)));
+    CKC(c, cudaMalloc(&c->nlinks, sizeof(int32_t) * 2 * ns));
+    CKC(c, cudaMalloc(&c->nflips, sizeof(int32_t) * 2 * ns));
     CKC(c, cudaMalloc(&c->diag, sizeof(double) * DIAG_N * ns));
-    CKC(c, cudaMemset(c->nlinks, 0, sizeof(int32_t) * ns));
-    CKC(c, cudaMemset(c->nflips, 0, sizeof(int32_t) * ns));
+    CKC(c, cudaMemset(c->nlinks, 0, sizeof(int32_t) * 2 * ns));
+    CKC(c, cudaMemset(c->nflips, 0, sizeof(int32_t) * 2 * ns));
     CKC(c, cudaMemset(c->diag, 0, sizeof(double) * DIAG_N * ns));
-    CKC(c, cudaMemcpy(c->pcur, c->hstate.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
-    CKC(c, cudaMemcpy(c->pnext, c->hstate.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
+    CKC(c, cudaMemcpy(c->pstate, c->hstate.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
+    CKC(c, cudaMemcpy(c->pstate + ns, c->hstate.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
     CKC(c, cudaMemcpy(c->pst, c->hst.data(), sizeof(PartStatic) * ns, cudaMemcpyHostToDevice));
     CKC(c, cudaMemcpy(c->dd + dom, &D, sizeof(DomDev), cudaMemcpyHostToDevice));
     c->links_total = lo;
@@ -665,8 +673,8 @@ int lbm_add_particles(lbm_ctx* c, int dom, int n, const lbm_particle* p) {
     // rasterise every particle at its current position (no link exchange, no
     // flips) and mark the work items near the particles for the next step
     CKC(c, cudaMemsetAsync(c->mark, 0xff, sizeof(int32_t) * 2 * std::max<int64_t>(1, c->total_items), c->stream));
-    CKC(c, cudaMemsetAsync(c->near_cnt, 0, sizeof(int32_t) * 2, c->stream));
-    CKC(c, launch_particle_links(c->kind, part_args(c, c->cur), PL_RASTER | PL_MARK, c->stream));
+    CKC(c, cudaMemsetAsync(c->near_cnt, 0, sizeof(int32_t) * 3, c->stream));
+    CKC(c, launch_particle_step(c->kind, part_args(c, c->cur), PL_RASTER | PL_MARK, c->stream));
     c->graph_dirty = true;
     return sync_and_check(c);
 }
@@ -795,7 +803,8 @@ int lbm_particles(lbm_ctx* c, int dom, lbm_particle* out, int cap) {
     const DomDev& D = c->hd[dom];
     if (D.np == 0) return 0;
     std::vector<PartState> s(D.np);
-    CKC(c, cudaMemcpyAsync(s.data(), c->pcur + D.p0, sizeof(PartState) * D.np, cudaMemcpyDeviceToHost, c->stream));
+    CKC(c, cudaMemcpyAsync(s.data(), c->pstate + (c->steps & 1) * c->np_slots + D.p0, sizeof(PartState) * D.np,
+                           cudaMemcpyDeviceToHost, c->stream));
     r = sync_and_check(c);
     if (r) return r;
     for (int i = 0; i < D.np && i < cap && out; ++i) {
@@ -865,16 +874,19 @@ int lbm_save(lbm_ctx* c, const char* path) {
         std::vector<PartState> s(ns);
         std::vector<int32_t> nl(ns), nf(ns), L(std::max<int64_t>(c->links_total, 1)), F(std::max<int64_t>(c->flips_total, 1));
         std::vector<double> dg(ns * DIAG_N);
-        ok = cudaMemcpy(s.data(), c->pcur, sizeof(PartState) * ns, cudaMemcpyDeviceToHost) == cudaSuccess &&
-             cudaMemcpy(nl.data(), c->nlinks, 4 * ns, cudaMemcpyDeviceToHost) == cudaSuccess &&
-             cudaMemcpy(nf.data(), c->nflips, 4 * ns, cudaMemcpyDeviceToHost) == cudaSuccess &&
-             cudaMemcpy(L.data(), c->links, 4 * L.size(), cudaMemcpyDeviceToHost) == cudaSuccess &&
-             cudaMemcpy(F.data(), c->flips, 4 * F.size(), cudaMemcpyDeviceToHost) == cudaSuccess &&
+        std::vector<double> fm(3 * std::max<int64_t>(c->flips_total, 1));
+        const int64_t pr = c->steps & 1;  // the lists of the current step
+        ok = cudaMemcpy(s.data(), c->pstate + pr * ns, sizeof(PartState) * ns, cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(fm.data(), c->flipmom + pr * 3 * c->flips_total, 8 * fm.size(), cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(nl.data(), c->nlinks + pr * ns, 4 * ns, cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(nf.data(), c->nflips + pr * ns, 4 * ns, cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(L.data(), c->links + pr * c->links_total, 4 * L.size(), cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(F.data(), c->flips + pr * c->flips_total, 4 * F.size(), cudaMemcpyDeviceToHost) == cudaSuccess &&
              cudaMemcpy(dg.data(), c->diag, 8 * dg.size(), cudaMemcpyDeviceToHost) == cudaSuccess;
         ok = ok && fwrite(c->hst.data(), sizeof(PartStatic), ns, fp) == ns && fwrite(s.data(), sizeof(PartState), ns, fp) == ns &&
              fwrite(nl.data(), 4, ns, fp) == ns && fwrite(nf.data(), 4, ns, fp) == ns &&
              fwrite(L.data(), 4, L.size(), fp) == L.size() && fwrite(F.data(), 4, F.size(), fp) == F.size() &&
-             fwrite(dg.data(), 8, dg.size(), fp) == dg.size();
+             fwrite(dg.data(), 8, dg.size(), fp) == dg.size() && fwrite(fm.data(), 8, fm.size(), fp) == fm.size();
     }
     ok = (fclose(fp) == 0) && ok;
     return ok ? LBM_OK : fail(c, LBM_E_IO, std::string("write failed: ") + path);
@@ -910,17 +922,18 @@ int lbm_load(lbm_ctx* c, const char* path) {
     std::vector<PartStatic> hst;
     std::vector<PartState> s;
     std::vector<int32_t> nl, nf, L, F;
-    std::vector<double> dg;
+    std::vector<double> dg, fm;
     if (np_total > 0) {
         const size_t ns = c->np_slots;
         hst.resize(ns); s.resize(ns); nl.resize(ns); nf.resize(ns);
         L.resize(std::max<int64_t>(h.links_total, 1));
         F.resize(std::max<int64_t>(h.flips_total, 1));
         dg.resize(ns * DIAG_N);
+        fm.resize(3 * std::max<int64_t>(h.flips_total, 1));
         bool ok = fread(hst.data(), sizeof(PartStatic), ns, fp) == ns && fread(s.data(), sizeof(PartState), ns, fp) == ns &&
                   fread(nl.data(), 4, ns, fp) == ns && fread(nf.data(), 4, ns, fp) == ns &&
                   fread(L.data(), 4, L.size(), fp) == L.size() && fread(F.data(), 4, F.size(), fp) == F.size() &&
-                  fread(dg.data(), 8, dg.size(), fp) == dg.size();
+                  fread(dg.data(), 8, dg.size(), fp) == dg.size() && fread(fm.data(), 8, fm.size(), fp) == fm.size();
         if (!ok) return bail("truncated checkpoint");
     }
     fclose(fp);
@@ -938,21 +951,23 @@ int lbm_load(lbm_ctx* c, const char* path) {
         free_particles(c);
         c->hst = hst;
         c->hstate = s;
-        CKC(c, cudaMalloc(&c->pcur, sizeof(PartState) * ns));
-        CKC(c, cudaMalloc(&c->pnext, sizeof(PartState) * ns));
+        CKC(c, cudaMalloc(&c->pstate, sizeof(PartState) * 2 * ns));
+        CKC(c, cudaMalloc(&c->flipmom, 2 * 8 * fm.size()));
         CKC(c, cudaMalloc(&c->pst, sizeof(PartStatic) * ns));
-        CKC(c, cudaMalloc(&c->links, 4 * L.size()));
-        CKC(c, cudaMalloc(&c->flips, 4 * F.size()));
-        CKC(c, cudaMalloc(&c->nlinks, 4 * ns));
-        CKC(c, cudaMalloc(&c->nflips, 4 * ns));
+        CKC(c, cudaMalloc(&c->links, 2 * 4 * L.size()));
+        CKC(c, cudaMalloc(&c->flips, 2 * 4 * F.size()));
+        CKC(c, cudaMalloc(&c->nlinks, 2 * 4 * ns));
+        CKC(c, cudaMalloc(&c->nflips, 2 * 4 * ns));
+        const int64_t pr = h.steps & 1;  // the lists of the restored step
         CKC(c, cudaMalloc(&c->diag, 8 * ns * DIAG_N));
-        CKC(c, cudaMemcpy(c->pcur, s.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
-        CKC(c, cudaMemcpy(c->pnext, s.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
+        CKC(c, cudaMemcpy(c->pstate, s.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
+        CKC(c, cudaMemcpy(c->pstate + ns, s.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
+        CKC(c, cudaMemcpy(c->flipmom + pr * fm.size(), fm.data(), 8 * fm.size(), cudaMemcpyHostToDevice));
         CKC(c, cudaMemcpy(c->pst, hst.data(), sizeof(PartStatic) * ns, cudaMemcpyHostToDevice));
-        CKC(c, cudaMemcpy(c->nlinks, nl.data(), 4 * ns, cudaMemcpyHostToDevice));
-        CKC(c, cudaMemcpy(c->nflips, nf.data(), 4 * ns, cudaMemcpyHostToDevice));
-        CKC(c, cudaMemcpy(c->links, L.data(), 4 * L.size(), cudaMemcpyHostToDevice));
-        CKC(c, cudaMemcpy(c->flips, F.data(), 4 * F.size(), cudaMemcpyHostToDevice));
+        CKC(c, cudaMemcpy(c->nlinks + pr * ns, nl.data(), 4 * ns, cudaMemcpyHostToDevice));
+        CKC(c, cudaMemcpy(c->nflips + pr * ns, nf.data(), 4 * ns, cudaMemcpyHostToDevice));
+        CKC(c, cudaMemcpy(c->links + pr * L.size(), L.data(), 4 * L.size(), cudaMemcpyHostToDevice));
+        CKC(c, cudaMemcpy(c->flips + pr * F.size(), F.data(), 4 * F.size(), cudaMemcpyHostToDevice));
         CKC(c, cudaMemcpy(c->diag, dg.data(), 8 * dg.size(), cudaMemcpyHostToDevice));
         c->links_total = h.links_total;
         c->flips_total = h.flips_total;
@@ -960,8 +975,8 @@ int lbm_load(lbm_ctx* c, const char* path) {
         c->np_active = np_total;
         CKC(c, cudaMemcpy(c->dd, c->hd.data(), sizeof(DomDev) * c->ndom, cudaMemcpyHostToDevice));
         CKC(c, cudaMemset(c->mark, 0xff, sizeof(int32_t) * 2 * std::max<int64_t>(1, c->total_items)));
-        CKC(c, cudaMemset(c->near_cnt, 0, sizeof(int32_t) * 2));
-        CKC(c, launch_particle_links(c->kind, part_args(c, c->cur), PL_MARK, c->stream));
+        CKC(c, cudaMemset(c->near_cnt, 0, sizeof(int32_t) * 3));
+        CKC(c, launch_particle_step(c->kind, part_args(c, c->cur), PL_MARK, c->stream));
         CKC(c, cudaStreamSynchronize(c->stream));
     }
     CKC(c, cudaMemcpy(c->dd, c->hd.data(), sizeof(DomDev) * c->ndom, cudaMemcpyHostToDevice));
@@ -984,11 +999,9 @@ int lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double* ms_out3, int64_t* laun
         if (parts) {
             const PartArgs a = part_args(c, c->cur);
             CKC(c, cudaEventRecord(ev[0], c->stream));
-            CKC(c, launch_particle_forces(c->kind, a, c->stream));
+            CKC(c, launch_particle_step(c->kind, a, PL_STEP, c->stream));
             CKC(c, cudaEventRecord(ev[1], c->stream));
-            CKC(c, launch_particle_links(c->kind, a, PL_SWAP | PL_ADVANCE | PL_RASTER | PL_MARK, c->stream));
-            CKC(c, cudaEventRecord(ev[2], c->stream));
-            launches += 2;
+            launches += 1;
         }
         CKC(c, cudaEventRecord(ev[3], c->stream));
         CKC(c, enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid));
@@ -999,8 +1012,6 @@ int lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double* ms_out3, int64_t* laun
         if (parts) {
             CKC(c, cudaEventElapsedTime(&ms, ev[0], ev[1]));
             acc[0] += ms;
-            CKC(c, cudaEventElapsedTime(&ms, ev[1], ev[2]));
-            acc[1] += ms;
         }
         CKC(c, cudaEventElapsedTime(&ms, ev[3], ev[4]));
         acc[2] += ms;

@@ -1,18 +1,25 @@
-// k_part.cu -- particle kernels of the D2Q9 hot path (arXiv:2006.12910 Sec. 3).
+// k_part.cu -- particle kernel of the D2Q9 hot path (arXiv:2006.12910 Sec. 3).
 //
-// One CTA per particle.  The stored populations are f*(t), post-collision.
-//  * k_particle_forces: Eq. MP1 over the boundary links of the rasterisation at
-//    t, the covered/uncovered-node force of Eq. MP3 for nodes that changed side
-//    at the previous re-rasterisation, the LJ-type repulsion of Eq. MP2, the
-//    totals of Eqs. MP3-MP4 (FP64, fixed-order block reduction) and the
-//    Newton-Euler update of Eqs. MP5-MP6 into the next-state slot.
-//  * k_particle_links: Eqs. MP7-MP8 as a pre-stream exchange: for the link
-//    r_v -> r_v + e_k the slot that r_v + e_k pulls next step receives
-//    f*_{-k}(r_v + e_k) + 2 rho0 omega_k (u_b . e_k) / c_s^2 and the slot r_v
-//    pulls receives f*_k(r_v) - the same, so the plain pull stream then
-//    realises the moving bounce-back on both sides.  It then commits the new
-//    state and re-rasterises: the new link list and the list of nodes that
-//    changed side (covered / uncovered), compacted in a fixed order.
+// One launch per timestep with two CTAs per particle that run side by side
+// (roles A and B below).  The stored populations are f*(t), post-collision;
+// the particle state and the link / flip lists are double-buffered by the
+// parity of the step, so A reads the lists of t while B writes those of t+1.
+// Role A (phases 1-2) and role B (phase 3):
+//  1. forces at t: Eq. MP1 over the boundary links of the rasterisation at t
+//     (each link's slots belong to this particle alone), the covered /
+//     uncovered-node force of Eq. MP3 from the node moments that the
+//     stream-collide pass of the previous step wrote while producing f*(t),
+//     and the LJ-type repulsion of Eq. MP2; FP64 totals (Eqs. MP3-MP4) and the
+//     Newton-Euler update of Eqs. MP5-MP6;
+//  2. Eqs. MP7-MP8 as a pre-stream exchange: for the link r_v -> r_v + e_k the
+//     slot that r_v + e_k pulls next receives f*_{-k}(r_v + e_k) +
+//     2 rho0 omega_k (u_b . e_k) / c_s^2 and the slot r_v pulls receives
+//     f*_k(r_v) minus the same, so the plain pull stream realises the moving
+//     bounce-back on both sides;
+//  3. re-rasterisation at r_c(t+1) = r_c(t) + U_p(t), which needs no force and
+//     therefore no other CTA's result: new link list, the nodes that change
+//     side (tagged for the next stream-collide pass), and the work items near
+//     the particle for the next step.
 #include "kernels.h"
 #include "lbm_dev.cuh"
 
@@ -117,35 +124,6 @@ __device__ __forceinline__ double full_pop(const typename S::T* base, const DomD
     return S::SHIFT ? v + wgt(i) * D.rho0 : v;
 }
 
-// Fixed-order block reduction of N doubles (deterministic for a fixed
-// blockDim).  Shuffle trees inside each warp with the N components
-// interleaved (FP64 latency is long on this part, so the adds of one level
-// are issued together), then lane c of warp 0 adds the per-warp results of
-// component c as a balanced tree.  The totals land in tot[0..N).
-template <int N>
-__device__ __forceinline__ void block_sum(double (&v)[N], double (*sh)[PBLOCK / 32], double* tot) {
-    static_assert(PBLOCK == 256, "the cross-warp tree below assumes 8 warps");
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        double t[N];
-#pragma unroll
-        for (int c = 0; c < N; ++c) t[c] = __shfl_down_sync(0xffffffffu, v[c], o);
-#pragma unroll
-        for (int c = 0; c < N; ++c) v[c] += t[c];
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int c = 0; c < N; ++c) sh[c][w] = v[c];
-    }
-    __syncthreads();
-    if (w == 0 && lane < N) {
-        const double* r = sh[lane];
-        tot[lane] = ((r[0] + r[1]) + (r[2] + r[3])) + ((r[4] + r[5]) + (r[6] + r[7]));
-    }
-    __syncthreads();
-}
-
 // Exclusive block scan of small non-negative counts; returns the block total.
 __device__ __forceinline__ int block_scan(int c, int* sh_warp, int& excl) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -220,336 +198,395 @@ __device__ __forceinline__ bool is_surface_f(const DomDev& D, const DiskF& k, in
     return false;
 }
 
-template <class S>
-__global__ void __launch_bounds__(PBLOCK) k_particle_forces(PartArgs a) {
-    const int p = blockIdx.x;
-    // The link kernel that follows appends the items near each particle for
-    // step t+1; empty that list first (its last reader finished a step ago).
-    if (p == 0 && threadIdx.x == 0 && a.near_cnt) a.near_cnt[(*a.ctr + 1) & 1] = 0;
-    const PartStatic st = a.st[p];
-    if (st.dom < 0) return;
-    const DomDev D = a.doms[st.dom];
-    if (p - D.p0 >= D.np) return;
-    const PartState q = a.cur[p];
-    const typename S::T* base = static_cast<const typename S::T*>(a.arena) + D.off;
-    const bool px = D.flags & FLAG_PX, py = D.flags & FLAG_PY;
-    __shared__ double sh[DIAG_N][PBLOCK / 32];
-    __shared__ double tot[DIAG_N];
-    __shared__ uint8_t bm[PB_CAP];
-    __shared__ double lj_fx[LJ_TAB], lj_fy[LJ_TAB];
-    __shared__ int lj_ox[LJ_TAB], lj_oy[LJ_TAB];
-    __shared__ int lj_n, nnear;
-    __shared__ int sh_warp[PBLOCK / 32];
-    __shared__ uint8_t wall_win[PB_CAP];
-    __shared__ int near[MAXNEAR];
-    __shared__ DiskF near_d[MAXNEAR];
-
-    double acc[DIAG_N];
-#pragma unroll
-    for (int c = 0; c < DIAG_N; ++c) acc[c] = 0.0;
-
-    // Eq. MP1: F = -2 [f'_k(r_v + e_k, t*) + rho0 omega_k (u_b . e_k) / c_s^2] e_k
-    const int nl = a.nlinks[p];
-    for (int l = threadIdx.x; l < nl; l += PBLOCK) {
-        const int32_t e = a.links[st.link_off + l];
-        const int node = e >> 3, k = (e & 7) + 1;
-        const int vy = node / D.pitch, vx = node - vy * D.pitch;
-        int fx = vx + cx(k), fy = vy + cy(k);
-        wrap_node(D, fx, fy);
-        const int ko = opp(k);
-        const double fo = full_pop<S>(base, D, ko, (int64_t)fy * D.pitch + fx);
-        const double bx = min_image((vx + 0.5 * cx(k)) - q.x, D.nx, px);
-        const double by = min_image((vy + 0.5 * cy(k)) - q.y, D.ny, py);
-        const double ubx = q.U - q.Om * by, uby = q.V + q.Om * bx;
-        const double ube = ubx * cx(k) + uby * cy(k);
-        const double s = -2.0 * (fo + D.rho0 * wgt(k) * ube * 3.0);
-        const double Fx = s * cx(k), Fy = s * cy(k);
-        acc[0] += Fx;
-        acc[1] += Fy;
-        acc[2] += bx * Fy - by * Fx;
-    }
-
-    // Covered (+) / uncovered (-) nodes: F = +- rho (u - U_p), u from f*(t).
-    const int nf = a.nflips[p];
-    for (int l = threadIdx.x; l < nf; l += PBLOCK) {
-        const int32_t e = a.flips[st.flip_off + l];
-        const int node = e >> 1;
-        const bool cov = e & 1;
-        const int y = node / D.pitch, x = node - y * D.pitch;
-        double r = 0.0, jx = 0.0, jy = 0.0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const double fi = full_pop<S>(base, D, i, node);
-            r += fi;
-            jx += fi * cx(i);
-            jy += fi * cy(i);
-        }
-        const double ux = (jx - 0.5 * r * D.gx) / r, uy = (jy - 0.5 * r * D.gy) / r;
-        const double sg = cov ? 1.0 : -1.0;
-        const double Fx = sg * r * (ux - q.U), Fy = sg * r * (uy - q.V);
-        const double rx = min_image(x - q.x, D.nx, px), ry = min_image(y - q.y, D.ny, py);
-        acc[3] += Fx;
-        acc[4] += Fy;
-        acc[5] += rx * Fy - ry * Fx;
-        if (cov) { acc[9] += 1.0; acc[11] += r; }
-        else { acc[10] += 1.0; acc[12] += r; }
-    }
-
-    // Eq. MP2 between surface nodes of p and surface nodes of the other
-    // particles of the domain, and between surface nodes of p and stationary
-    // solid / wall nodes, within the threshold r_it.
-    if (D.lj_psi != 0.0) {
-        const double R = st.R;
-        const Box b = disk_box(q.x, q.y, R);
-        const Box e = {b.x0 - 1, b.y0 - 1, b.w + 2, b.h + 2};
-        const int reach = (int)floor(D.lj_rit);
-        const bool use_bm = e.n() <= PB_CAP;
-        // Offset table of Eq. MP2 (built once on the host for this domain).
-        if (threadIdx.x == 0) lj_n = a.lj_cnt[st.dom];
-        for (int t = threadIdx.x; t < LJ_TAB; t += PBLOCK) {
-            const LjEntry en = a.lj_tab[(int64_t)st.dom * LJ_TAB + t];
-            lj_ox[t] = en.ox;
-            lj_oy[t] = en.oy;
-            lj_fx[t] = en.fx;
-            lj_fy[t] = en.fy;
-        }
-        near_list(a, D, p, a.cur, q.x, q.y, R, D.lj_rit + 4.0, near, near_d, &nnear, sh_warp);
-        if (use_bm) {
-            const DiskF kf = make_diskf(q.x, q.y, R);
-            for (int t = threadIdx.x; t < e.n(); t += PBLOCK)
-                bm[t] = inside_f(D, kf, e.x0 + t % e.w, e.y0 + t / e.w, false) ? 1 : 0;
-        }
-        // Solid / wall status of every node within r_it of the box, staged once:
-        // 1 = wall or solid node, 0 = fluid or outside an open end.
-        const Box W = {b.x0 - reach, b.y0 - reach, b.w + 2 * reach, b.h + 2 * reach};
-        const bool use_win = W.n() <= PB_CAP;
-        if (use_win) {
-            for (int t = threadIdx.x; t < W.n(); t += PBLOCK) {
-                int wx = W.x0 + t % W.w, wy = W.y0 + t / W.w;
-                uint8_t v = 0;
-                if ((D.flags & FLAG_WY) && (wy < 0 || wy >= D.ny)) v = 1;
-                else if (wrap_node(D, wx, wy)) v = a.solid[D.node_off + (int64_t)wy * D.pitch + wx] != 0;
-                wall_win[t] = v;
-            }
-        }
-        __syncthreads();
-        const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
-        for (int t = threadIdx.x; t < b.n(); t += PBLOCK) {
-            const int ay = b.y0 + t / b.w, ax = b.x0 + t % b.w;
-            bool surf;
-            if (use_bm) {
-                const int c = (ay - e.y0) * e.w + (ax - e.x0);
-                surf = bm[c] != 0;
-                if (surf) {
-                    bool all_in = true;
-#pragma unroll
-                    for (int i = 1; i < 9; ++i) all_in &= bm[c + cy(i) * e.w + cx(i)] != 0;
-                    surf = !all_in;
-                }
-            } else {
-                surf = is_surface(D, q.x, q.y, R, ax, ay);
-            }
-            if (!surf) continue;
-            double rax = 0.0, ray = 0.0;
-            bool arm = false;  // torque arm of this surface node, computed on first use
-            for (int j = 0; j < nn; ++j) {
-                const DiskF& ko = near_d[j];
-                // only surface nodes of p within r_it of the other disk's rim can pair
-                const float ddx = (float)wrap_off(ax - ko.cx, D.nx, px) - ko.fx;
-                const float ddy = (float)wrap_off(ay - ko.cy, D.ny, py) - ko.fy;
-                const float lim = (float)(ko.R + D.lj_rit) + 2.0f;
-                if (ddx * ddx + ddy * ddy > lim * lim) continue;
-                for (int w = 0; w < lj_n; ++w) {
-                    // node b = a + o expressed in the other particle's own frame
-                    const int bx = ko.cx + wrap_off(ax + lj_ox[w] - ko.cx, D.nx, px);
-                    const int by = ko.cy + wrap_off(ay + lj_oy[w] - ko.cy, D.ny, py);
-                    if (!is_surface_f(D, ko, bx, by)) continue;
-                    // repulsion on a from b = a + o, the table entry of o
-                    if (!arm) { rax = min_image(ax - q.x, D.nx, px); ray = min_image(ay - q.y, D.ny, py); arm = true; }
-                    acc[6] += lj_fx[w];
-                    acc[7] += lj_fy[w];
-                    acc[8] += rax * lj_fy[w] - ray * lj_fx[w];
-                }
-            }
-#pragma unroll 1
-            for (int j = 0; j < lj_n; ++j) {
-                int wx = ax + lj_ox[j], wy = ay + lj_oy[j];
-                bool wall;
-                if (use_win) {
-                    wall = wall_win[(wy - W.y0) * W.w + (wx - W.x0)] != 0;
-                } else if ((D.flags & FLAG_WY) && (wy < 0 || wy >= D.ny)) {
-                    wall = true;
-                } else {
-                    if (!wrap_node(D, wx, wy)) continue;
-                    wall = a.solid[D.node_off + (int64_t)wy * D.pitch + wx] != 0;
-                }
-                if (!wall) continue;
-                if (!arm) { rax = min_image(ax - q.x, D.nx, px); ray = min_image(ay - q.y, D.ny, py); arm = true; }
-                acc[6] += lj_fx[j];
-                acc[7] += lj_fy[j];
-                acc[8] += rax * lj_fy[j] - ray * lj_fx[j];
-            }
-        }
-    }
-
-    block_sum<DIAG_N>(acc, sh, tot);
-    if (threadIdx.x < DIAG_N) a.diag[(int64_t)p * DIAG_N + threadIdx.x] = tot[threadIdx.x];
-    if (threadIdx.x == 0) {
-        // Eqs. MP5, MP6; r_c(t+1) = r_c(t) + U_p(t).
-        PartState n = q;
-        if (!st.fixed) {
-            const double Fx = (tot[0] + tot[3]) + tot[6], Fy = (tot[1] + tot[4]) + tot[7];
-            const double T = (tot[2] + tot[5]) + tot[8];
-            n.U = q.U + Fx * st.inv_m + st.buoy * D.gx;
-            n.V = q.V + Fy * st.inv_m + st.buoy * D.gy;
-            n.Om = q.Om + T * st.inv_I;
-            n.x = q.x + q.U;
-            n.y = q.y + q.V;
-            n.th = q.th + q.Om;
-            if (px) n.x = n.x - D.nx * floor(n.x / D.nx);
-            if (py) n.y = n.y - D.ny * floor(n.y / D.ny);
-        }
-        a.next[p] = n;
-    }
+// Position at t+1 from the state at t (Sec. 3: r_c(t+1) = r_c(t) + U_p(t)).
+__device__ __forceinline__ void next_position(const DomDev& D, const PartState& q, bool fixed, double& x, double& y) {
+    if (fixed) { x = q.x; y = q.y; return; }
+    x = q.x + q.U;
+    y = q.y + q.V;
+    if (D.flags & FLAG_PX) x = x - D.nx * floor(x / D.nx);
+    if (D.flags & FLAG_PY) y = y - D.ny * floor(y / D.ny);
 }
 
+// Fixed-order block sum of the components [c0, c1) of v (deterministic for a
+// fixed blockDim).  FP64 issue rate is low on this part, so the tree first
+// halves across warps in shared memory (4, 2, 1 warps active) and only then
+// shuffles inside warp 0; the totals land in tot[c].
+template <int N>
+__device__ __forceinline__ void block_sum_range(double (&v)[N], int c0, int c1, double* buf, double* tot) {
+    static_assert(PBLOCK == 256, "tree below assumes 256 threads");
+#pragma unroll
+    for (int c = 0; c < N; ++c)
+        if (c >= c0 && c < c1) buf[c * PBLOCK + threadIdx.x] = v[c];
+    __syncthreads();
+    for (int h = PBLOCK / 2; h >= 32; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+#pragma unroll
+            for (int c = 0; c < N; ++c)
+                if (c >= c0 && c < c1) buf[c * PBLOCK + threadIdx.x] += buf[c * PBLOCK + threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            if (c < c0 || c >= c1) continue;
+            double x = buf[c * PBLOCK + threadIdx.x];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (threadIdx.x == 0) tot[c] = x;
+        }
+    }
+    __syncthreads();
+}
+
+// Shared memory of one CTA; role A and role B use disjoint parts of a union.
+struct SmemA {
+    double red[DIAG_N * PBLOCK];
+    uint8_t bm[PB_CAP];
+    uint8_t wall_win[PB_CAP];
+    double lj_fx[LJ_TAB], lj_fy[LJ_TAB];
+    int lj_ox[LJ_TAB], lj_oy[LJ_TAB];
+};
+struct SmemB {
+    uint8_t bnew[PB_CAP], bold[PB_CAP], node_st[PB_CAP];
+};
+union SmemU {
+    SmemA A;
+    SmemB B;
+};
+
 template <class S>
-__global__ void __launch_bounds__(PBLOCK) k_particle_links(PartArgs a, int modes) {
-    const bool swap = modes & PL_SWAP, advance = modes & PL_ADVANCE;
+__global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes) {
     typedef typename S::A A;
-    const int p = blockIdx.x;
+    const bool role_b = (int)blockIdx.x >= a.np;
+    const int p = role_b ? blockIdx.x - a.np : blockIdx.x;
+    const int64_t t = *a.ctr;
+    const bool advance = modes & PL_ADVANCE;
+    // The near-item list of step t+2 is touched by nobody during this step.
+    if (blockIdx.x == 0 && threadIdx.x == 0 && advance) a.near_cnt[(t + 2) % 3] = 0;
+    if (role_b ? !(modes & (PL_RASTER | PL_MARK)) : !(modes & (PL_FORCES | PL_SWAP | PL_ADVANCE))) return;
     const PartStatic st = a.st[p];
     if (st.dom < 0) return;
     const DomDev D = a.doms[st.dom];
     if (p - D.p0 >= D.np) return;
-    const PartState q = a.cur[p];
-    typename S::T* base = static_cast<typename S::T*>(a.arena) + D.off;
+    const int par = (int)(t & 1);
+    const PartState* S0 = a.state + (int64_t)par * a.np;
+    const PartState q = S0[p];
+    const double R = st.R;
     const bool px = D.flags & FLAG_PX, py = D.flags & FLAG_PY;
+    typename S::T* base = static_cast<typename S::T*>(a.arena) + D.off;
+    double nxp = q.x, nyp = q.y;
+    if (advance) next_position(D, q, st.fixed, nxp, nyp);
+
+    __shared__ __align__(16) unsigned char smem_raw[sizeof(SmemU)];
+    SmemU& sm = *reinterpret_cast<SmemU*>(smem_raw);
+    __shared__ double tot[DIAG_N];
+    __shared__ int lj_n, nnear;
     __shared__ int sh_warp[PBLOCK / 32];
-    __shared__ uint8_t bnew[PB_CAP], bold[PB_CAP], node_st[PB_CAP];
     __shared__ int near[MAXNEAR];
     __shared__ DiskF near_d[MAXNEAR];
-    __shared__ int nnear;
 
-    // Eqs. MP7-MP8 on the links of the rasterisation at t with u_b(t).
-    if (swap) {
-        const int nl = a.nlinks[p];
-        const A scl = (A)D.scale, inv = (A)D.inv_scale;
-        for (int l = threadIdx.x; l < nl; l += PBLOCK) {
-            const int32_t e = a.links[st.link_off + l];
-            const int node = e >> 3, k = (e & 7) + 1;
-            const int vy = node / D.pitch, vx = node - vy * D.pitch;
-            int fx = vx + cx(k), fy = vy + cy(k);
-            wrap_node(D, fx, fy);
-            const double bx = min_image((vx + 0.5 * cx(k)) - q.x, D.nx, px);
-            const double by = min_image((vy + 0.5 * cy(k)) - q.y, D.ny, py);
-            const double ubx = q.U - q.Om * by, uby = q.V + q.Om * bx;
-            const A corr = (A)(2.0 * D.rho0 * wgt(k) * (ubx * cx(k) + uby * cy(k)) * 3.0);
-            typename S::T* sa = base + (int64_t)k * D.plane + node;                          // pulled by r_v + e_k
-            typename S::T* sb = base + (int64_t)opp(k) * D.plane + (int64_t)fy * D.pitch + fx;  // pulled by r_v
-            const A va = to_a(*sa, inv), vb = to_a(*sb, inv);
-            from_a(vb + corr, scl, *sa);
-            from_a(va - corr, scl, *sb);
+    if (!role_b) {
+        // ------------------------------------------------------------------ role A
+        const int32_t* links = a.links + (int64_t)par * a.links_total;
+        const int32_t* flips = a.flips + (int64_t)par * a.flips_total;
+        const int nl = a.nlinks[(int64_t)par * a.np + p];
+        const int nf = a.nflips[(int64_t)par * a.np + p];
+        double acc[DIAG_N];
+#pragma unroll
+        for (int c = 0; c < DIAG_N; ++c) acc[c] = 0.0;
+        bool lj_on = false;
+        if (modes & PL_FORCES) {
+            // Eq. MP1: F = -2 [f'_k(r_v + e_k, t*) + rho0 omega_k (u_b . e_k) / c_s^2] e_k
+            for (int l = threadIdx.x; l < nl; l += PBLOCK) {
+                const int32_t e = links[st.link_off + l];
+                const int node = e >> 3, k = (e & 7) + 1;
+                const int vy = node / D.pitch, vx = node - vy * D.pitch;
+                int fx = vx + cx(k), fy = vy + cy(k);
+                wrap_node(D, fx, fy);
+                const double fo = full_pop<S>(base, D, opp(k), (int64_t)fy * D.pitch + fx);
+                const double bx = min_image((vx + 0.5 * cx(k)) - q.x, D.nx, px);
+                const double by = min_image((vy + 0.5 * cy(k)) - q.y, D.ny, py);
+                const double ubx = q.U - q.Om * by, uby = q.V + q.Om * bx;
+                const double ube = ubx * cx(k) + uby * cy(k);
+                const double s = -2.0 * (fo + D.rho0 * wgt(k) * ube * 3.0);
+                const double Fx = s * cx(k), Fy = s * cy(k);
+                acc[0] += Fx;
+                acc[1] += Fy;
+                acc[2] += bx * Fy - by * Fx;
+            }
+            // Covered (+) / uncovered (-) nodes: F = +- rho (u - U_p), with rho and
+            // sum f* e of the node at t written by the previous stream-collide pass.
+            for (int l = threadIdx.x; l < nf; l += PBLOCK) {
+                const int32_t e = flips[st.flip_off + l];
+                const int node = e >> 1;
+                const bool cov = e & 1;
+                const int y = node / D.pitch, x = node - y * D.pitch;
+                const double* m = a.flipmom + 3 * ((int64_t)par * a.flips_total + st.flip_off + l);
+                const double r = m[0], jx = m[1], jy = m[2];
+                const double ux = (jx - 0.5 * r * D.gx) / r, uy = (jy - 0.5 * r * D.gy) / r;
+                const double sg = cov ? 1.0 : -1.0;
+                const double Fx = sg * r * (ux - q.U), Fy = sg * r * (uy - q.V);
+                const double rx = min_image(x - q.x, D.nx, px), ry = min_image(y - q.y, D.ny, py);
+                acc[3] += Fx;
+                acc[4] += Fy;
+                acc[5] += rx * Fy - ry * Fx;
+                if (cov) { acc[9] += 1.0; acc[11] += r; }
+                else { acc[10] += 1.0; acc[12] += r; }
+            }
+            // Eq. MP2 between surface nodes of p and surface nodes of the other
+            // particles, and between surface nodes of p and stationary solid /
+            // wall nodes, within the threshold r_it.
+            if (D.lj_psi != 0.0) {
+                near_list(a, D, p, S0, q.x, q.y, R, D.lj_rit + 4.0, near, near_d, &nnear, sh_warp);
+                const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
+                const Box b = disk_box(q.x, q.y, R);
+                const Box e = {b.x0 - 1, b.y0 - 1, b.w + 2, b.h + 2};
+                const int reach = (int)floor(D.lj_rit);
+                const bool use_bm = e.n() <= PB_CAP;
+                // 1 = wall or solid node within reach of the box, 0 = fluid or beyond an open end
+                const Box W = {b.x0 - reach, b.y0 - reach, b.w + 2 * reach, b.h + 2 * reach};
+                const bool use_win = W.n() <= PB_CAP;
+                int any_wall = 0;
+                for (int i = threadIdx.x; i < W.n(); i += PBLOCK) {
+                    int wx = W.x0 + i % W.w, wy = W.y0 + i / W.w;
+                    uint8_t v = 0;
+                    if ((D.flags & FLAG_WY) && (wy < 0 || wy >= D.ny)) v = 1;
+                    else if (wrap_node(D, wx, wy)) v = a.solid[D.node_off + (int64_t)wy * D.pitch + wx] != 0;
+                    if (use_win) sm.A.wall_win[i] = v;
+                    any_wall |= v;
+                }
+                lj_on = __syncthreads_or(any_wall) || nn > 0 || !use_win;
+                if (lj_on) {
+                    if (threadIdx.x == 0) lj_n = a.lj_cnt[st.dom];
+                    for (int i = threadIdx.x; i < LJ_TAB; i += PBLOCK) {
+                        const LjEntry en = a.lj_tab[(int64_t)st.dom * LJ_TAB + i];
+                        sm.A.lj_ox[i] = en.ox;
+                        sm.A.lj_oy[i] = en.oy;
+                        sm.A.lj_fx[i] = en.fx;
+                        sm.A.lj_fy[i] = en.fy;
+                    }
+                    if (use_bm) {
+                        const DiskF kf = make_diskf(q.x, q.y, R);
+                        for (int i = threadIdx.x; i < e.n(); i += PBLOCK)
+                            sm.A.bm[i] = inside_f(D, kf, e.x0 + i % e.w, e.y0 + i / e.w, false) ? 1 : 0;
+                    }
+                    __syncthreads();
+                    for (int i = threadIdx.x; i < b.n(); i += PBLOCK) {
+                        const int ay = b.y0 + i / b.w, ax = b.x0 + i % b.w;
+                        bool surf;
+                        if (use_bm) {
+                            const int c = (ay - e.y0) * e.w + (ax - e.x0);
+                            surf = sm.A.bm[c] != 0;
+                            if (surf) {
+                                bool all_in = true;
+#pragma unroll
+                                for (int k = 1; k < 9; ++k) all_in &= sm.A.bm[c + cy(k) * e.w + cx(k)] != 0;
+                                surf = !all_in;
+                            }
+                        } else {
+                            surf = is_surface(D, q.x, q.y, R, ax, ay);
+                        }
+                        if (!surf) continue;
+                        double rax = 0.0, ray = 0.0;
+                        bool arm = false;  // torque arm of this surface node, computed on first use
+                        for (int j = 0; j < nn; ++j) {
+                            const DiskF& ko = near_d[j];
+                            const float ddx = (float)wrap_off(ax - ko.cx, D.nx, px) - ko.fx;
+                            const float ddy = (float)wrap_off(ay - ko.cy, D.ny, py) - ko.fy;
+                            const float lim = (float)(ko.R + D.lj_rit) + 2.0f;
+                            if (ddx * ddx + ddy * ddy > lim * lim) continue;
+                            for (int w = 0; w < lj_n; ++w) {
+                                // node b = a + o expressed in the other particle's own frame
+                                const int bx = ko.cx + wrap_off(ax + sm.A.lj_ox[w] - ko.cx, D.nx, px);
+                                const int by = ko.cy + wrap_off(ay + sm.A.lj_oy[w] - ko.cy, D.ny, py);
+                                if (!is_surface_f(D, ko, bx, by)) continue;
+                                if (!arm) { rax = min_image(ax - q.x, D.nx, px); ray = min_image(ay - q.y, D.ny, py); arm = true; }
+                                acc[6] += sm.A.lj_fx[w];
+                                acc[7] += sm.A.lj_fy[w];
+                                acc[8] += rax * sm.A.lj_fy[w] - ray * sm.A.lj_fx[w];
+                            }
+                        }
+#pragma unroll 1
+                        for (int j = 0; j < lj_n; ++j) {
+                            int wx = ax + sm.A.lj_ox[j], wy = ay + sm.A.lj_oy[j];
+                            bool wall;
+                            if (use_win) {
+                                wall = sm.A.wall_win[(wy - W.y0) * W.w + (wx - W.x0)] != 0;
+                            } else if ((D.flags & FLAG_WY) && (wy < 0 || wy >= D.ny)) {
+                                wall = true;
+                            } else {
+                                if (!wrap_node(D, wx, wy)) continue;
+                                wall = a.solid[D.node_off + (int64_t)wy * D.pitch + wx] != 0;
+                            }
+                            if (!wall) continue;
+                            if (!arm) { rax = min_image(ax - q.x, D.nx, px); ray = min_image(ay - q.y, D.ny, py); arm = true; }
+                            acc[6] += sm.A.lj_fx[j];
+                            acc[7] += sm.A.lj_fy[j];
+                            acc[8] += rax * sm.A.lj_fy[j] - ray * sm.A.lj_fx[j];
+                        }
+                    }
+                }
+            }
+            // component groups: links 0-2, covered/uncovered 3-5 and 9-12, LJ 6-8
+            if (threadIdx.x < DIAG_N) tot[threadIdx.x] = 0.0;
+            __syncthreads();
+            if (nl > 0) block_sum_range<DIAG_N>(acc, 0, 3, sm.A.red, tot);
+            if (nf > 0) {
+                block_sum_range<DIAG_N>(acc, 3, 6, sm.A.red, tot);
+                block_sum_range<DIAG_N>(acc, 9, 13, sm.A.red, tot);
+            }
+            if (lj_on) block_sum_range<DIAG_N>(acc, 6, 9, sm.A.red, tot);
+            if (threadIdx.x < DIAG_N) a.diag[(int64_t)p * DIAG_N + threadIdx.x] = tot[threadIdx.x];
         }
+        // Eqs. MP7-MP8 on the links of the rasterisation at t with u_b(t); every
+        // read of these slots above happened before this barrier.
         __syncthreads();
+        if (modes & PL_SWAP) {
+            const A scl = (A)D.scale, inv = (A)D.inv_scale;
+            for (int l = threadIdx.x; l < nl; l += PBLOCK) {
+                const int32_t e = links[st.link_off + l];
+                const int node = e >> 3, k = (e & 7) + 1;
+                const int vy = node / D.pitch, vx = node - vy * D.pitch;
+                int fx = vx + cx(k), fy = vy + cy(k);
+                wrap_node(D, fx, fy);
+                const double bx = min_image((vx + 0.5 * cx(k)) - q.x, D.nx, px);
+                const double by = min_image((vy + 0.5 * cy(k)) - q.y, D.ny, py);
+                const double ubx = q.U - q.Om * by, uby = q.V + q.Om * bx;
+                const A corr = (A)(2.0 * D.rho0 * wgt(k) * (ubx * cx(k) + uby * cy(k)) * 3.0);
+                typename S::T* sa = base + (int64_t)k * D.plane + node;                          // pulled by r_v + e_k
+                typename S::T* sb = base + (int64_t)opp(k) * D.plane + (int64_t)fy * D.pitch + fx;  // pulled by r_v
+                const A va = to_a(*sa, inv), vb = to_a(*sb, inv);
+                from_a(vb + corr, scl, *sa);
+                from_a(va - corr, scl, *sb);
+            }
+        }
+        if (advance && threadIdx.x == 0) {
+            // Eqs. MP5, MP6 (velocities) with r_c(t+1) = r_c(t) + U_p(t).
+            PartState n = q;
+            if (!st.fixed) {
+                if (modes & PL_FORCES) {
+                    const double Fx = (tot[0] + tot[3]) + tot[6], Fy = (tot[1] + tot[4]) + tot[7];
+                    const double T = (tot[2] + tot[5]) + tot[8];
+                    n.U = q.U + Fx * st.inv_m + st.buoy * D.gx;
+                    n.V = q.V + Fy * st.inv_m + st.buoy * D.gy;
+                    n.Om = q.Om + T * st.inv_I;
+                }
+                n.x = nxp;
+                n.y = nyp;
+                n.th = q.th + q.Om;
+                if (fabs(q.U) >= 1.0 || fabs(q.V) >= 1.0) atomicOr(a.err, ERR_STATE);  // faster than a node per step
+            }
+            a.state[(int64_t)(par ^ 1) * a.np + p] = n;
+        }
+        return;
     }
 
-    const PartState n = advance ? a.next[p] : q;
-    const PartState* others = advance ? a.next : a.cur;
-    const double R = st.R;
+    // ---------------------------------------------------------------------- role B
+    const int64_t t_next = advance ? t + 1 : t;
+    const int wpar = (int)(t_next & 1);
     if (modes & PL_MARK) {
-        // Work items (row segments) within two nodes of the disk's box at the
-        // step the state is about to reach are "near": the stream-collide pass
-        // of that step runs them only after this particle's link exchange.
-        const int64_t t_mark = advance ? *a.ctr + 1 : *a.ctr;
-        const int par = (int)(t_mark & 1);
-        const Box bm2 = disk_box(n.x, n.y, R);
+        // Work items (row segments) within two nodes of the disk's boxes at t
+        // and t+1 are "near": the stream-collide pass of that step runs them
+        // after this kernel, and they hold every node that changes side.
+        const int mpar = (int)(t_next & 1);
+        const int lpar = (int)(t_next % 3);
+        const Box bo = disk_box(q.x, q.y, R), bn = disk_box(nxp, nyp, R);
+        const int x0 = min(bo.x0, bn.x0) - 2, x1 = max(bo.x0 + bo.w, bn.x0 + bn.w) + 1;
+        const int y0 = min(bo.y0, bn.y0) - 2, y1 = max(bo.y0 + bo.h, bn.y0 + bn.h) + 1;
         const int seg_w = 32 * D.V;
-        const int xs = bm2.x0 - 2, xe = bm2.x0 + bm2.w + 1;
-        for (int r = threadIdx.x; r < bm2.h + 4; r += PBLOCK) {
-            int y = bm2.y0 - 2 + r, xdummy = 0;
+        for (int r = threadIdx.x; r <= y1 - y0; r += PBLOCK) {
+            int y = y0 + r, xdummy = 0;
             if (!wrap_node(D, xdummy, y)) continue;
-            for (int xx = xs;; xx += seg_w) {
-                const int xc = xx < xe ? xx : xe;
+            for (int xx = x0;; xx += seg_w) {
+                const int xc = xx < x1 ? xx : x1;
                 int x = xc, yd = 0;
                 if (wrap_node(D, x, yd)) {
                     const int64_t item = D.item_off + (int64_t)y * D.seg_per_row + x / seg_w;
-                    int32_t* m = a.mark + (int64_t)par * a.total_items + item;
-                    if (atomicExch(m, (int32_t)t_mark) != (int32_t)t_mark) {
-                        const int slot = atomicAdd(a.near_cnt + par, 1);
-                        a.near_list[(int64_t)par * a.total_items + slot] = (int32_t)item;
+                    int32_t* m = a.mark + (int64_t)mpar * a.total_items + item;
+                    if (atomicExch(m, (int32_t)t_next) != (int32_t)t_next) {
+                        const int slot = atomicAdd(a.near_cnt + lpar, 1);
+                        a.near_list[(int64_t)lpar * a.total_items + slot] = (int32_t)item;
                     }
                 }
-                if (xc == xe) break;
+                if (xc == x1) break;
             }
         }
     }
-    if (!(modes & PL_RASTER)) {
-        if (advance && threadIdx.x == 0) a.cur[p] = n;
-        return;
+    if (!(modes & PL_RASTER)) return;
+
+    // Particles whose disks at t+1 may touch this one's: they bound the exterior
+    // nodes of the new links and reveal overlaps.
+    near_list(a, D, p, S0, q.x, q.y, R, 6.0, near, near_d, &nnear, sh_warp);
+    const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
+    if (nnear > MAXNEAR && threadIdx.x == 0) atomicOr(a.err, ERR_STATE);
+    if (threadIdx.x < nn) {
+        const int p2 = near[threadIdx.x];
+        const PartState o = S0[p2];
+        double ox = o.x, oy = o.y;
+        if (advance) next_position(D, o, a.st[p2].fixed, ox, oy);
+        near_d[threadIdx.x] = make_diskf(ox, oy, a.st[p2].R);
     }
     // Union of the old and new boxes; every neighbour of a node inside either
     // disk lies in it.
-    const Box bo = disk_box(q.x, q.y, R), bn = disk_box(n.x, n.y, R);
+    const Box bo = disk_box(q.x, q.y, R), bn = disk_box(nxp, nyp, R);
     Box U;
     U.x0 = min(bo.x0, bn.x0);
     U.y0 = min(bo.y0, bn.y0);
     U.w = max(bo.x0 + bo.w, bn.x0 + bn.w) - U.x0;
     U.h = max(bo.y0 + bo.h, bn.y0 + bn.h) - U.y0;
     const bool use_bm = U.n() <= PB_CAP;
-    near_list(a, D, p, others, n.x, n.y, R, 4.0, near, near_d, &nnear, sh_warp);
-    const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
-    if (nnear > MAXNEAR && threadIdx.x == 0) atomicOr(a.err, ERR_STATE);
     if (use_bm) {
-        const DiskF kn = make_diskf(n.x, n.y, R), ko = make_diskf(q.x, q.y, R);
-        for (int t = threadIdx.x; t < U.n(); t += PBLOCK) {
-            const int xu = U.x0 + t % U.w, yu = U.y0 + t / U.w;
-            bnew[t] = inside_f(D, kn, xu, yu, true) ? 1 : 0;
-            bold[t] = advance ? (inside_f(D, ko, xu, yu, true) ? 1 : 0) : bnew[t];
+        const DiskF kn = make_diskf(nxp, nyp, R), ko = make_diskf(q.x, q.y, R);
+        for (int i = threadIdx.x; i < U.n(); i += PBLOCK) {
+            const int xu = U.x0 + i % U.w, yu = U.y0 + i / U.w;
+            sm.B.bnew[i] = inside_f(D, kn, xu, yu, true) ? 1 : 0;
+            sm.B.bold[i] = advance ? (inside_f(D, ko, xu, yu, true) ? 1 : 0) : sm.B.bnew[i];
             // 0 = fluid node in the domain, 1 = solid, 2 = outside an open end
             int x = xu, y = yu;
-            node_st[t] = wrap_node(D, x, y) ? (a.solid[D.node_off + (int64_t)y * D.pitch + x] ? 1 : 0) : 2;
+            sm.B.node_st[i] = wrap_node(D, x, y) ? (a.solid[D.node_off + (int64_t)y * D.pitch + x] ? 1 : 0) : 2;
         }
     }
     __syncthreads();
     auto in_new = [&](int xu, int yu) -> bool {
-        if (use_bm) return bnew[(yu - U.y0) * U.w + (xu - U.x0)] != 0;
+        if (use_bm) return sm.B.bnew[(yu - U.y0) * U.w + (xu - U.x0)] != 0;
         int x = xu, y = yu;
         if (!wrap_node(D, x, y)) { x = xu; y = yu; }
-        return inside_disk(D, n.x, n.y, R, x, y);
+        return inside_disk(D, nxp, nyp, R, x, y);
     };
     auto in_old = [&](int xu, int yu) -> bool {
-        if (use_bm) return bold[(yu - U.y0) * U.w + (xu - U.x0)] != 0;
+        if (use_bm) return sm.B.bold[(yu - U.y0) * U.w + (xu - U.x0)] != 0;
         int x = xu, y = yu;
         if (!wrap_node(D, x, y)) { x = xu; y = yu; }
         return inside_disk(D, q.x, q.y, R, x, y);
     };
-
-    // New link list and nodes that changed side, in a fixed (row-major, lane) order.
+    int32_t* links = a.links + (int64_t)wpar * a.links_total;
+    int32_t* flips = a.flips + (int64_t)wpar * a.flips_total;
+    const int64_t stamp = (int64_t)(int32_t)(t + 1) << 32;
     int ltotal = 0, ftotal = 0;
     bool overlap = false;
     for (int t0 = 0; t0 < U.n(); t0 += PBLOCK) {
-        const int t = t0 + threadIdx.x;
+        const int i = t0 + threadIdx.x;
         uint32_t mask = 0;
         int node = 0, fcode = 0, fc = 0;
-        if (t < U.n()) {
-            const int xu = U.x0 + t % U.w, yu = U.y0 + t / U.w;
+        if (i < U.n()) {
+            const int xu = U.x0 + i % U.w, yu = U.y0 + i / U.w;
             int x = xu, y = yu;
             if (wrap_node(D, x, y)) {
                 node = y * D.pitch + x;
-                const bool solid_here = use_bm ? node_st[t] == 1 : a.solid[D.node_off + node] != 0;
+                const bool solid_here = use_bm ? sm.B.node_st[i] == 1 : a.solid[D.node_off + node] != 0;
                 const bool now = in_new(xu, yu);
                 if (now) {
                     for (int j = 0; j < nn; ++j)
                         if (inside_f(D, near_d[j], xu, yu, true)) overlap = true;
                     if (!solid_here) {
-#pragma unroll
+#pragma unroll 1
                         for (int k = 1; k < 9; ++k) {
                             const int fxu = xu + cx(k), fyu = yu + cy(k);
-                            int fx = fxu, fy = fyu;
                             if (use_bm) {
-                                if (node_st[(fyu - U.y0) * U.w + (fxu - U.x0)] != 0) continue;
+                                if (sm.B.node_st[(fyu - U.y0) * U.w + (fxu - U.x0)] != 0) continue;
                             } else {
+                                int fx = fxu, fy = fyu;
                                 if (!wrap_node(D, fx, fy)) continue;
                                 if (a.solid[D.node_off + (int64_t)fy * D.pitch + fx]) continue;
                             }
@@ -566,25 +603,29 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_links(PartArgs a, int modes
             }
         }
         int excl;
-        const int c = __popc(mask);
-        const int tot = block_scan(c, sh_warp, excl);
+        const int tot_l = block_scan(__popc(mask), sh_warp, excl);
         int w = ltotal + excl;
         for (int k = 1; k < 9; ++k)
             if (mask & (1u << k)) {
-                if (w < st.link_cap) a.links[st.link_off + w] = (node << 3) | (k - 1);
+                if (w < st.link_cap) links[st.link_off + w] = (node << 3) | (k - 1);
                 ++w;
             }
-        ltotal += tot;
+        ltotal += tot_l;
         int fex;
-        const int ftot = block_scan(fc, sh_warp, fex);
-        if (fc && ftotal + fex < st.flip_cap) a.flips[st.flip_off + ftotal + fex] = fcode;
-        ftotal += ftot;
+        const int tot_f = block_scan(fc, sh_warp, fex);
+        if (fc && ftotal + fex < st.flip_cap) {
+            const int64_t idx = st.flip_off + ftotal + fex;
+            flips[idx] = fcode;
+            // the stream-collide pass of this step leaves this node's moments in flipmom[slot]
+            const int64_t slot = (int64_t)wpar * a.flips_total + idx;
+            a.fliptag[D.node_off + node] = stamp | (uint32_t)slot;
+        }
+        ftotal += tot_f;
     }
     if (overlap || ltotal > st.link_cap || ftotal > st.flip_cap) atomicOr(a.err, ERR_STATE);
     if (threadIdx.x == 0) {
-        a.nlinks[p] = ltotal < st.link_cap ? ltotal : st.link_cap;
-        a.nflips[p] = ftotal < st.flip_cap ? ftotal : st.flip_cap;
-        if (advance) a.cur[p] = n;
+        a.nlinks[(int64_t)wpar * a.np + p] = ltotal < st.link_cap ? ltotal : st.link_cap;
+        a.nflips[(int64_t)wpar * a.np + p] = ftotal < st.flip_cap ? ftotal : st.flip_cap;
     }
 }
 
@@ -598,15 +639,9 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_links(PartArgs a, int modes
         default: return cudaErrorInvalidValue;        \
     }
 
-cudaError_t launch_particle_forces(int kind, const PartArgs& a, cudaStream_t s) {
+cudaError_t launch_particle_step(int kind, const PartArgs& a, int modes, cudaStream_t s) {
     if (a.np <= 0) return cudaSuccess;
-    LBM_PDISPATCH(kind, (k_particle_forces<S><<<a.np, PBLOCK, 0, s>>>(a)));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_particle_links(int kind, const PartArgs& a, int modes, cudaStream_t s) {
-    if (a.np <= 0) return cudaSuccess;
-    LBM_PDISPATCH(kind, (k_particle_links<S><<<a.np, PBLOCK, 0, s>>>(a, modes)));
+    LBM_PDISPATCH(kind, (k_particle_step<S><<<2 * a.np, PBLOCK, 0, s>>>(a, modes)));
     return cudaGetLastError();
 }
 

@@ -89,6 +89,30 @@ __device__ __forceinline__ void load_flags(const uint16_t* p, uint16_t (&fl)[V])
     }
 }
 
+// Moments of a node that changes side this step (tag stamped step + 1): rho
+// and sum f* e of the populations just stored, read back in the storage
+// format so they equal what a later read of the arena would give.
+template <class S>
+__device__ __noinline__ void flip_moments(const StreamArgs& a, const DomDev& D, int y, int x,
+                                          const typename S::T* obase, int32_t stamp) {
+    const int64_t ni = (int64_t)y * D.pitch + x;
+    const int64_t tag = a.fliptag[D.node_off + ni];
+    if ((int32_t)(tag >> 32) != stamp) return;
+    const uint32_t slot = (uint32_t)tag;
+    double r = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        double v = (double)to_a(obase[(int64_t)i * D.plane + ni], (typename S::A)D.inv_scale);
+        if (S::SHIFT) v += wgt(i) * D.rho0;
+        r += v;
+        jx += v * cx(i);
+        jy += v * cy(i);
+    }
+    a.flipmom[3 * (int64_t)slot + 0] = r;
+    a.flipmom[3 * (int64_t)slot + 1] = jx;
+    a.flipmom[3 * (int64_t)slot + 2] = jy;
+}
+
 template <class S, bool NOISE, bool PL>
 __global__ void __launch_bounds__(512) k_stream_collide(StreamArgs a) {
     typedef typename S::T T;
@@ -103,12 +127,20 @@ __global__ void __launch_bounds__(512) k_stream_collide(StreamArgs a) {
     const T* __restrict__ src = static_cast<const T*>(a.src);
     T* __restrict__ dst = static_cast<T*>(a.dst);
     bool ok = true;
-    const int64_t count = a.mode == STREAM_NEAR ? (int64_t)__ldg(a.near_cnt + par) : a.total_items;
+    const int lpar = (int)(step64 % 3);
+    const int64_t count = a.mode == STREAM_NEAR ? (int64_t)__ldg(a.near_cnt + lpar) : a.total_items;
+    const int32_t next_stamp = (int32_t)(step64 + 1);
 
     for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < count; w += nwarps) {
         int64_t g = w;
-        if (a.mode == STREAM_NEAR) g = __ldg(a.near_list + (int64_t)par * a.total_items + w);
-        else if (a.mode == STREAM_FAR && __ldg(a.mark + (int64_t)par * a.total_items + w) == (int32_t)step64) continue;
+        bool near_item;
+        if (a.mode == STREAM_NEAR) {
+            g = __ldg(a.near_list + (int64_t)lpar * a.total_items + w);
+            near_item = true;
+        } else {
+            near_item = __ldg(a.mark + (int64_t)par * a.total_items + w) == (int32_t)step64;
+            if (a.mode == STREAM_FAR && near_item) continue;
+        }
         const int d = a.ndom == 1 ? 0 : find_domain(a.item_off, a.ndom, g);
         const DomDev& D = a.doms[d];
         const int nx = D.nx, ny = D.ny, flags = D.flags;
@@ -125,7 +157,10 @@ __global__ void __launch_bounds__(512) k_stream_collide(StreamArgs a) {
         if (x0 + V > nx) {  // ragged tail chunk
 #pragma unroll 1
             for (int k = 0; k < V; ++k)
-                if (x0 + k < nx) ok &= slow_node<S, NOISE, PL>(D, P, x0 + k, y, base, obase, a.solid, step);
+                if (x0 + k < nx) {
+                    ok &= slow_node<S, NOISE, PL>(D, P, x0 + k, y, base, obase, a.solid, step);
+                    if (near_item) flip_moments<S>(a, D, y, x0 + k, obase, next_stamp);
+                }
             continue;
         }
         const A inv = P.inv_scale;
@@ -202,6 +237,10 @@ __global__ void __launch_bounds__(512) k_stream_collide(StreamArgs a) {
         }
 #pragma unroll
         for (int i = 0; i < 9; ++i) store_vec<S>(obase + (int64_t)i * plane + y * pitch + x0, f[i], P.scale);
+        if (near_item) {
+#pragma unroll 1
+            for (int k = 0; k < V; ++k) flip_moments<S>(a, D, y, x0 + k, obase, next_stamp);
+        }
     }
     if (!ok) atomicOr(a.err, ERR_UNSTABLE);
 }

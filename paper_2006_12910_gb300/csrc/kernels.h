@@ -23,11 +23,16 @@ struct StreamArgs {
     unsigned* err;            // sticky device error bits
     // Work selection: STREAM_ALL every item; STREAM_FAR the items not marked
     // near a particle for this step (mark[step & 1][item] != step);
-    // STREAM_NEAR the items in near_list[step & 1][0 .. near_cnt[step & 1]).
+    // STREAM_NEAR the items in near_list[step % 3][0 .. near_cnt[step % 3]).
     int mode;
     const int32_t* mark;      // [2][total_items]
-    const int32_t* near_list; // [2][total_items]
-    const int32_t* near_cnt;  // [2]
+    const int32_t* near_list; // [3][total_items]
+    const int32_t* near_cnt;  // [3]
+    // Nodes that change side this step: a node whose tag carries step + 1
+    // gets rho, sum f* e_x, sum f* e_y of its new populations written to
+    // flipmom[3 * slot] (only work items near particles are looked at).
+    const int64_t* fliptag;
+    double* flipmom;
 };
 enum { STREAM_ALL = 0, STREAM_FAR = 1, STREAM_NEAR = 2 };
 
@@ -53,34 +58,37 @@ cudaError_t launch_checks(int kind, const DomDev& D, const void* arena, const ui
                           int nblocks, double* out, cudaStream_t s);
 constexpr int CHECK_BLOCKS = 304;
 
-// ---- particle kernels (k_part.cu) ----
+// ---- particle kernel (k_part.cu) ----
 struct PartArgs {
     const DomDev* doms;
-    void* arena;               // populations holding f*(t) (read by forces, swapped by links)
+    void* arena;               // populations holding f*(t) (read for forces, link slots exchanged)
     const uint8_t* solid;
-    PartState* cur;            // state at t (updated to t+1 by the commit phase)
-    PartState* next;           // state at t+1 written by the force phase
+    PartState* state;          // [2][np]: state at step t in slot (t & 1)
     const PartStatic* st;
     int np;
-    int32_t* links;            // per particle: (node << 3) | (k - 1), node = y*pitch + x of r_v
-    int32_t* nlinks;
-    int32_t* flips;            // per particle: (node << 1) | covered
-    int32_t* nflips;
+    // link / flip lists, two copies by step parity: copy (t & 1) holds the
+    // rasterisation at t, the other receives that of t+1
+    int32_t* links;            // [2][links_total]: (node << 3) | (k - 1), node = y*pitch + x of r_v
+    int32_t* nlinks;           // [2][np]
+    int32_t* flips;            // [2][flips_total]: (node << 1) | covered
+    int32_t* nflips;           // [2][np]
+    int64_t links_total, flips_total;
+    double* flipmom;           // [2][flips_total][3]: rho, sum f* e_x, sum f* e_y at the step of use
+    int64_t* fliptag;          // per node: (step << 32) | flip slot, for the stream-collide pass
     double* diag;              // np * DIAG_N
     unsigned* err;
-    // near-item bookkeeping for the overlapped step (see StreamArgs)
     const int64_t* ctr;        // step counter of the state in `arena`
     int32_t* mark;             // [2][total_items]
-    int32_t* near_list;        // [2][total_items]
-    int32_t* near_cnt;         // [2]
+    int32_t* near_list;        // [3][total_items]
+    int32_t* near_cnt;         // [3]
     int64_t total_items;
     const LjEntry* lj_tab;     // [ndom][LJ_TAB], valid entries first
     const int32_t* lj_cnt;     // [ndom]
 };
-// Link-kernel modes: exchange the link slots, advance the state, rebuild the
-// link / flip lists, mark the work items near each particle for the next step.
-enum { PL_SWAP = 1, PL_ADVANCE = 2, PL_RASTER = 4, PL_MARK = 8 };
-cudaError_t launch_particle_forces(int kind, const PartArgs& a, cudaStream_t s);
-cudaError_t launch_particle_links(int kind, const PartArgs& a, int modes, cudaStream_t s);
+// Particle-step modes: forces + Newton-Euler, exchange of the link slots,
+// advance to t+1, rebuild of the link / flip lists, marking of the near items.
+enum { PL_FORCES = 1, PL_SWAP = 2, PL_ADVANCE = 4, PL_RASTER = 8, PL_MARK = 16 };
+constexpr int PL_STEP = PL_FORCES | PL_SWAP | PL_ADVANCE | PL_RASTER | PL_MARK;
+cudaError_t launch_particle_step(int kind, const PartArgs& a, int modes, cudaStream_t s);
 
 }  // namespace lbmk
