@@ -306,6 +306,7 @@ cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int bloc
     a.ctr_out = c->ctr + (cur ^ 1);
     a.err = c->err;
     a.mode = mode;
+    a.flips = c->np_active > 0 && mode != STREAM_FAR;
     a.mark = c->mark;
     a.near_list = c->near_list;
     a.near_cnt = c->near_cnt;
@@ -1037,30 +1038,29 @@ int lbm_autotune(lbm_ctx* c, int trial_steps) {
     CKC(c, cudaEventCreate(&e1));
     float best = 1e30f;
     int best_block = c->block, best_mode = c->grid_mode;
-    const int save_block = c->block, save_mode = c->grid_mode;
-    for (int mode = 0; mode < 2; ++mode)
-        for (int b : blocks) {
-            c->block = b;
-            c->grid_mode = mode;
-            set_launch(c);
-            cudaError_t e = enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid);
-            if (e != cudaSuccess) continue;
-            cudaEventRecord(e0, c->stream);
-            for (int s = 0; s < trial_steps && e == cudaSuccess; ++s)
-                e = enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid);
-            cudaEventRecord(e1, c->stream);
-            if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) continue;
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; best_block = b; best_mode = mode; }
-        }
+    {
+        for (int mode = 0; mode < 2; ++mode)
+            for (int b : blocks) {
+                c->block = b;
+                c->grid_mode = mode;
+                set_launch(c);
+                cudaError_t e = enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid);
+                if (e != cudaSuccess) continue;
+                cudaEventRecord(e0, c->stream);
+                for (int s = 0; s < trial_steps && e == cudaSuccess; ++s)
+                    e = enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid);
+                cudaEventRecord(e1, c->stream);
+                if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) continue;
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; best_block = b; best_mode = mode; }
+            }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->block = best_block;
     c->grid_mode = best_mode;
     set_launch(c);
-    (void)save_block;
-    (void)save_mode;
     return sync_and_check(c);
 }
 

@@ -113,7 +113,75 @@ __device__ __noinline__ void flip_moments(const StreamArgs& a, const DomDev& D, 
     a.flipmom[3 * (int64_t)slot + 2] = jy;
 }
 
-template <class S, bool NOISE, bool PL>
+// Everything after the pull of one V-node chunk: bounce-back and Zou-He
+// patches from the per-node flag words (special chunks only), collision,
+// 16-byte stores, and the moments of nodes that change side (near items).
+template <class S, bool NOISE, bool PL, bool FLIPS>
+__device__ __forceinline__ bool finish_chunk(const StreamArgs& a, const DomDev& D, const Prm<typename S::A>& P,
+                                             typename S::A (&f)[9][S::V], bool special, int y, int x0,
+                                             const typename S::T* base, typename S::T* obase, uint32_t step,
+                                             bool near_item, int32_t next_stamp) {
+    typedef typename S::A A;
+    constexpr int V = S::V;
+    const int64_t pitch = D.pitch, plane = D.plane;
+    const int nx = D.nx;
+    const A inv = P.inv_scale;
+    bool ok = true;
+    uint32_t solid_bits = 0;
+    if (special) {
+        uint16_t fl[V];
+        load_flags<V>(a.nflags + D.node_off + (int64_t)y * pitch + x0, fl);
+        uint32_t any = 0;
+#pragma unroll
+        for (int k = 0; k < V; ++k) any |= fl[k];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            if (any & (1u << i)) {  // halfway bounce-back: the node's own opposite slot
+                A own[V];
+                load_vec<S>(base + (int64_t)opp(i) * plane + y * pitch + x0, own, inv);
+#pragma unroll
+                for (int k = 0; k < V; ++k)
+                    if (fl[k] & (1u << i)) f[i][k] = own[k];
+            }
+        }
+        if (any & (NF_ZH_IN | NF_ZH_OUT)) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                if (fl[k] & (NF_ZH_IN | NF_ZH_OUT)) {
+                    A n9[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) n9[i] = f[i][k];
+                    if (fl[k] & NF_ZH_IN) zou_he<A>(n9, 0, P.rho_in, P.d_in);
+                    else zou_he<A>(n9, 1, P.rho_out, P.d_out);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) f[i][k] = n9[i];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            if (fl[k] & NF_SOLID) solid_bits |= 1u << k;
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        A n9[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) n9[i] = f[i][k];
+        const bool sol = (solid_bits >> k) & 1u;
+        if (!sol) ok &= collide_node<A, S::SHIFT, NOISE, PL>(n9, P, (uint32_t)(y * nx + x0 + k), step);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i][k] = sol ? (A)0 : n9[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) store_vec<S>(obase + (int64_t)i * plane + y * pitch + x0, f[i], P.scale);
+    if (FLIPS && near_item) {
+#pragma unroll 1
+        for (int k = 0; k < V; ++k) flip_moments<S>(a, D, y, x0 + k, obase, next_stamp);
+    }
+    return ok;
+}
+
+template <class S, bool NOISE, bool PL, bool FLIPS>
 __global__ void __launch_bounds__(512) k_stream_collide(StreamArgs a) {
     typedef typename S::T T;
     typedef typename S::A A;
@@ -133,14 +201,9 @@ __global__ void __launch_bounds__(512) k_stream_collide(StreamArgs a) {
 
     for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < count; w += nwarps) {
         int64_t g = w;
-        bool near_item;
-        if (a.mode == STREAM_NEAR) {
-            g = __ldg(a.near_list + (int64_t)lpar * a.total_items + w);
-            near_item = true;
-        } else {
-            near_item = __ldg(a.mark + (int64_t)par * a.total_items + w) == (int32_t)step64;
-            if (a.mode == STREAM_FAR && near_item) continue;
-        }
+        int32_t mark = (int32_t)step64;
+        if (a.mode == STREAM_NEAR) g = __ldg(a.near_list + (int64_t)lpar * a.total_items + w);
+        else mark = __ldg(a.mark + (int64_t)par * a.total_items + w);  // consumed after the descriptor loads
         const int d = a.ndom == 1 ? 0 : find_domain(a.item_off, a.ndom, g);
         const DomDev& D = a.doms[d];
         const int nx = D.nx, ny = D.ny, flags = D.flags;
@@ -150,6 +213,8 @@ __global__ void __launch_bounds__(512) k_stream_collide(StreamArgs a) {
         const int seg = local - y * D.seg_per_row;
         const int x0 = (seg * 32 + lane) * V;
         const uint32_t word = __ldg(a.special + D.mask_off + (int64_t)y * D.seg_per_row + seg);
+        const bool near_item = mark == (int32_t)step64;
+        if (a.mode == STREAM_FAR && near_item) continue;
         if (x0 >= nx) continue;
         const Prm<A> P = load_prm<A>(D);
         const T* base = src + D.off;
@@ -159,7 +224,7 @@ __global__ void __launch_bounds__(512) k_stream_collide(StreamArgs a) {
             for (int k = 0; k < V; ++k)
                 if (x0 + k < nx) {
                     ok &= slow_node<S, NOISE, PL>(D, P, x0 + k, y, base, obase, a.solid, step);
-                    if (near_item) flip_moments<S>(a, D, y, x0 + k, obase, next_stamp);
+                    if (FLIPS && near_item) flip_moments<S>(a, D, y, x0 + k, obase, next_stamp);
                 }
             continue;
         }
@@ -190,68 +255,27 @@ __global__ void __launch_bounds__(512) k_stream_collide(StreamArgs a) {
                 f[i][V - 1] = load_one<S>(p + xr, inv);
             }
         }
-        uint32_t solid_bits = 0;
-        if ((word >> lane) & 1u) {
-            uint16_t fl[V];
-            load_flags<V>(a.nflags + D.node_off + (int64_t)y * pitch + x0, fl);
-            uint32_t any = 0;
-#pragma unroll
-            for (int k = 0; k < V; ++k) any |= fl[k];
-#pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                if (any & (1u << i)) {  // halfway bounce-back: the node's own opposite slot
-                    A own[V];
-                    load_vec<S>(base + (int64_t)opp(i) * plane + y * pitch + x0, own, inv);
-#pragma unroll
-                    for (int k = 0; k < V; ++k)
-                        if (fl[k] & (1u << i)) f[i][k] = own[k];
-                }
-            }
-            if (any & (NF_ZH_IN | NF_ZH_OUT)) {
-#pragma unroll
-                for (int k = 0; k < V; ++k) {
-                    if (fl[k] & (NF_ZH_IN | NF_ZH_OUT)) {
-                        A n9[9];
-#pragma unroll
-                        for (int i = 0; i < 9; ++i) n9[i] = f[i][k];
-                        if (fl[k] & NF_ZH_IN) zou_he<A>(n9, 0, P.rho_in, P.d_in);
-                        else zou_he<A>(n9, 1, P.rho_out, P.d_out);
-#pragma unroll
-                        for (int i = 0; i < 9; ++i) f[i][k] = n9[i];
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < V; ++k)
-                if (fl[k] & NF_SOLID) solid_bits |= 1u << k;
-        }
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            A n9[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) n9[i] = f[i][k];
-            const bool sol = (solid_bits >> k) & 1u;
-            if (!sol) ok &= collide_node<A, S::SHIFT, NOISE, PL>(n9, P, (uint32_t)(y * nx + x0 + k), step);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) f[i][k] = sol ? (A)0 : n9[i];
-        }
-#pragma unroll
-        for (int i = 0; i < 9; ++i) store_vec<S>(obase + (int64_t)i * plane + y * pitch + x0, f[i], P.scale);
-        if (near_item) {
-#pragma unroll 1
-            for (int k = 0; k < V; ++k) flip_moments<S>(a, D, y, x0 + k, obase, next_stamp);
-        }
+        ok &= finish_chunk<S, NOISE, PL, FLIPS>(a, D, P, f, ((word >> lane) & 1u) != 0, y, x0, base, obase, step,
+                                                near_item, next_stamp);
     }
     if (!ok) atomicOr(a.err, ERR_UNSTABLE);
 }
 
+template <class S, bool FLIPS>
+static cudaError_t launch_kind_f(bool noise, bool pl, const StreamArgs& a, int block, int64_t grid, cudaStream_t s) {
+    if (noise && pl) k_stream_collide<S, true, true, FLIPS><<<(unsigned)grid, block, 0, s>>>(a);
+    else if (noise) k_stream_collide<S, true, false, FLIPS><<<(unsigned)grid, block, 0, s>>>(a);
+    else if (pl) k_stream_collide<S, false, true, FLIPS><<<(unsigned)grid, block, 0, s>>>(a);
+    else k_stream_collide<S, false, false, FLIPS><<<(unsigned)grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// The variant that writes the moments of nodes changing side runs the items
+// near particles (mode STREAM_NEAR, or STREAM_ALL when particles exist).
 template <class S>
 static cudaError_t launch_kind(bool noise, bool pl, const StreamArgs& a, int block, int64_t grid, cudaStream_t s) {
-    if (noise && pl) k_stream_collide<S, true, true><<<(unsigned)grid, block, 0, s>>>(a);
-    else if (noise) k_stream_collide<S, true, false><<<(unsigned)grid, block, 0, s>>>(a);
-    else if (pl) k_stream_collide<S, false, true><<<(unsigned)grid, block, 0, s>>>(a);
-    else k_stream_collide<S, false, false><<<(unsigned)grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+    if (a.flips) return launch_kind_f<S, true>(noise, pl, a, block, grid, s);
+    return launch_kind_f<S, false>(noise, pl, a, block, grid, s);
 }
 
 cudaError_t launch_stream_collide(int kind, bool noise, bool pl, const StreamArgs& a, int block, int64_t grid,

@@ -25,6 +25,7 @@ struct StreamArgs {
     // near a particle for this step (mark[step & 1][item] != step);
     // STREAM_NEAR the items in near_list[step % 3][0 .. near_cnt[step % 3]).
     int mode;
+    int flips;                // 1: also write the moments of tagged nodes (items near particles)
     const int32_t* mark;      // [2][total_items]
     const int32_t* near_list; // [3][total_items]
     const int32_t* near_cnt;  // [3]
