@@ -264,8 +264,10 @@ def main():
     alg_bytes = fluid * 2 * 9 * S  # read 9 + write 9 populations per fluid node update
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (k1_ms * 1e-3) / 1e9
+    launch = ctx.launch()
+    k1_name = "k_stream_staged" if launch[0] == 2 else "k_stream_collide"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_stream_collide", "peak_source": peak_kind,
+                "traffic": None, "kernel": k1_name, "peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "kernel_ms": k1_ms,
                 "kernel_share": kk / max(kf + kl + kk, 1e-9),
                 "particle_kernel_ms": kf / args.profile_steps,
@@ -337,7 +339,8 @@ def main():
                            "nodes": nodes, "fluid_nodes": fluid, "store": args.store,
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                            "l2": "no flush; per-step footprint (2 arenas) exceeds the 129 MB L2",
-                           "launch": {"block": None, "graph_steps": 8}},
+                           "launch": {"kernel": k1_name, "block": launch[1], "stages": launch[2],
+                                      "grid": launch[3], "graph_steps": 8}},
                 "clocks": clk, "gpu_launches": args.steps * kernels_per_step,
                 "roofline": roofline, "e2e": e2e, "variants": variants, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -171,10 +171,24 @@ int64_t lbm_step_count(const lbm_ctx* ctx);
 int lbm_save(lbm_ctx* ctx, const char* path);
 int lbm_load(lbm_ctx* ctx, const char* path);
 
-/* Pick the stream-and-collide launch shape (warps per block, rows per warp
- * item) by short timed trials on the context's own data; the state is saved
- * and restored around the trials. */
+/* Pick the stream-and-collide kernel and launch shape (kernel, threads per
+ * block and stages as in lbm_set_launch) by short timed trials on the
+ * context's own data.  The trials write only the second population arena,
+ * which the next step overwrites, so the state and step count are unchanged. */
 int lbm_autotune(lbm_ctx* ctx, int trial_steps);
+
+/* Launch configuration of the stream-and-collide kernel (no paper
+ * counterpart; it selects among equivalent implementations of Eqs. e.LB1 /
+ * e.LB2, all with the same results).  kernel: 0 register-pipelined with one
+ * warp item per warp, 1 the same with a persistent grid-stride grid, 2 staged
+ * through shared memory with bulk asynchronous copies (`stages` row segments
+ * in flight per warp, 1..8; block at most 256 threads).  block: threads per
+ * CTA, a multiple of 32 in [32, 512].  LBM_E_INVAL for values out of range
+ * or a staged configuration whose shared memory does not fit an SM; the
+ * previous configuration then stays.  lbm_get_launch writes {kernel, block,
+ * stages, grid} to out4. */
+int lbm_set_launch(lbm_ctx* ctx, int32_t kernel, int32_t block, int32_t stages);
+int lbm_get_launch(const lbm_ctx* ctx, int64_t* out4);
 
 /* Measurement: advance nsteps timesteps with plain launches in sequence (no
  * graph, no overlap) and a CUDA-event pair around every kernel on the

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_NAME = "liblbm_gb300.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
-UNITS = ["k_stream.cu", "k_aux.cu", "k_part.cu", "capi.cu", "k_noalloc.cu"]
+UNITS = ["k_stream.cu", "k_staged.cu", "k_aux.cu", "k_part.cu", "capi.cu", "k_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

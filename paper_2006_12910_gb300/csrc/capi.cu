@@ -88,7 +88,8 @@ struct lbm_ctx {
     int cur = 0;
     int64_t steps = 0;
     int block = 256;
-    int grid_mode = 0;  // 0: one warp item per warp; 1: persistent grid-stride
+    int grid_mode = 0;  // 0: one warp item per warp; 1: persistent grid-stride; 2: staged kernel
+    int stages = 0;     // row segments in flight per warp of the staged kernel
     int64_t grid = 1;
 
     double* d_stage = nullptr;
@@ -155,7 +156,8 @@ void fill_dom(DomDev& D, const lbm_params& p, int kind) {
               (p.inlet_outlet ? FLAG_IO : 0);
     D.V = store_vector_width(kind);
     D.pitch = (int32_t)round_up(p.nx, std::max<int64_t>(D.V, 128 / (int64_t)elem_bytes(kind)));
-    D.plane = (int64_t)D.pitch * p.ny;
+    // y walls: one ghost row on each side of every plane (bounce-back mailboxes)
+    D.plane = (int64_t)D.pitch * (p.ny + (p.walls_y ? 2 : 0));
     const int nchunks = (p.nx + D.V - 1) / D.V;
     D.seg_per_row = (nchunks + 31) / 32;
     D.seed = p.seed;
@@ -191,45 +193,63 @@ void fill_dom(DomDev& D, const lbm_params& p, int kind) {
     D.n_pl_f = (float)D.n_pl; D.xi_pl_f = (float)D.xi_pl; D.tau_min_f = (float)D.tau_min;
     D.tau_max_f = (float)D.tau_max; D.tmin_pow_f = (float)D.tmin_pow; D.tmax_pow_f = (float)D.tmax_pow;
     D.scale_f = (float)D.scale; D.inv_scale_f = (float)D.inv_scale;
+    D.hot_d.omega = 1.0 / p.tau;
+    D.hot_d.om = 1.0 - 1.0 / p.tau;
+    D.hot_d.tgx = p.tau * p.gx;
+    D.hot_d.tgy = p.tau * p.gy;
+    D.hot_d.rho0 = p.rho0;
+    D.hot_d.scale = D.scale;
+    D.hot_d.inv_scale = D.inv_scale;
+    D.hot_d.pad = 0.0;
+    D.hot_f.omega = (float)D.hot_d.omega;
+    D.hot_f.om = (float)D.hot_d.om;
+    D.hot_f.tgx = (float)D.hot_d.tgx;
+    D.hot_f.tgy = (float)D.hot_d.tgy;
+    D.hot_f.rho0 = (float)p.rho0;
+    D.hot_f.scale = (float)D.scale;
+    D.hot_f.inv_scale = (float)D.inv_scale;
+    D.hot_f.pad = 0.0f;
 }
 
-// Per-node flag words and per-chunk bits.  Flag bit i (1..8) marks a pulled
-// direction that bounces back: its source lies beyond a y wall, is a solid
-// node, or lies outside the x range at a wall-corner node of open ends.  Open
-// columns carry the Zou-He bits; solid nodes NF_SOLID.  A chunk bit is set
-// when any of its nodes has a nonzero flag word.
+// Per-node flag words and per-chunk bits (mailbox bounce-back).  Flag bit j
+// (1..8) marks a fluid node whose neighbour x + e_j is solid or lies in a
+// ghost row beyond a y wall (x wrapped when periodic; beyond an open end
+// there is no neighbour); the node writes its f*_j into that neighbour's slot
+// opp(j) after each collision.  Open columns carry the Zou-He bits, except on
+// wall rows, whose end nodes carry NF_CORNER (their sources beyond the x
+// range reflect from the node's own opposite slot); solid nodes NF_SOLID.  A
+// chunk bit is set when any of its nodes has a nonzero flag word.
 void build_flags(const DomDev& D, const uint8_t* solid, std::vector<uint16_t>& fl, std::vector<uint32_t>& words) {
     fl.assign((size_t)D.plane, 0);
     words.assign((size_t)D.ny * D.seg_per_row, 0u);
-    const bool px = D.flags & FLAG_PX, py = D.flags & FLAG_PY, wy = D.flags & FLAG_WY, io = D.flags & FLAG_IO;
+    const bool px = D.flags & FLAG_PX, wy = D.flags & FLAG_WY, io = D.flags & FLAG_IO;
     static const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     static const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     for (int y = 0; y < D.ny; ++y)
         for (int x = 0; x < D.nx; ++x) {
             uint16_t f = 0;
-            const bool corner_row = wy && (y == 0 || y == D.ny - 1);
+            const bool wall_row = wy && (y == 0 || y == D.ny - 1);
             if (solid[(size_t)y * D.nx + x]) {
                 f = NF_SOLID;
             } else {
-                for (int i = 1; i < 9; ++i) {
-                    int sx = x - ex[i], sy = y - ey[i];
-                    bool bb = false, unknown = false;
-                    if (sy < 0 || sy >= D.ny) {
-                        if (wy) bb = true;
-                        else sy = (sy + D.ny) % D.ny;
+                for (int j = 1; j < 9; ++j) {
+                    int tx = x + ex[j], ty = y + ey[j];
+                    bool ghost = false;
+                    if (ty < 0 || ty >= D.ny) {
+                        if (wy) ghost = true;
+                        else ty = (ty + D.ny) % D.ny;
                     }
-                    if (!bb && (sx < 0 || sx >= D.nx)) {
-                        if (px) sx = (sx + D.nx) % D.nx;
-                        else if (corner_row) bb = true;
-                        else unknown = true;
+                    if (tx < 0 || tx >= D.nx) {
+                        if (!px) continue;
+                        tx = (tx + D.nx) % D.nx;
                     }
-                    if (!bb && !unknown && solid[(size_t)sy * D.nx + sx]) bb = true;
-                    if (bb) f |= (uint16_t)(1u << i);
+                    if (ghost || solid[(size_t)ty * D.nx + tx]) f |= (uint16_t)(1u << j);
                 }
-                if (io && !corner_row && x == 0) f |= NF_ZH_IN;
-                if (io && !corner_row && x == D.nx - 1) f |= NF_ZH_OUT;
+                if (io && (x == 0 || x == D.nx - 1)) {
+                    if (wall_row) f |= NF_CORNER;
+                    else f |= x == 0 ? NF_ZH_IN : NF_ZH_OUT;
+                }
             }
-            (void)py;
             fl[(size_t)y * D.pitch + x] = f;
             if (f) {
                 const int c = x / D.V;
@@ -244,7 +264,18 @@ void set_launch(lbm_ctx* c) {
     const int64_t wpb = c->block / 32;
     int64_t full = (c->total_items + wpb - 1) / wpb;
     if (full < 1) full = 1;
-    if (c->grid_mode == 1) {
+    if (c->grid_mode == 2) {
+        // Staged kernel: as many warps as fit, trimmed so that the items
+        // split into equal whole shares per warp (less tail imbalance).
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int bps = staged_blocks_per_sm(c->kind, c->noise, c->pl, c->block, c->stages);
+        const int64_t max_warps = std::max<int64_t>(1, (int64_t)sms * std::max(bps, 1) * wpb);
+        const int64_t share = (c->total_items + max_warps - 1) / max_warps;
+        const int64_t warps = (c->total_items + share - 1) / std::max<int64_t>(share, 1);
+        c->grid = std::max<int64_t>(1, (warps + wpb - 1) / wpb);
+    } else if (c->grid_mode == 1) {
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -312,7 +343,7 @@ cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int bloc
     a.near_cnt = c->near_cnt;
     a.fliptag = c->fliptag;
     a.flipmom = c->flipmom;
-    return launch_stream_collide(c->kind, c->noise, c->pl, a, block, grid, s);
+    return launch_stream_collide(c->kind, c->noise, c->pl, a, block, grid, c->grid_mode == 2 ? c->stages : 0, s);
 }
 
 // One timestep.  With particles the stream-collide items away from every
@@ -439,7 +470,7 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
     for (int d = 0; d < ndom; ++d) {
         DomDev& D = c->hd[d];
         fill_dom(D, per_domain[d], c->kind);
-        D.off = off;
+        D.off = off + (per_domain[d].walls_y ? D.pitch : 0);  // row 0 of plane 0, after the ghost row
         D.node_off = node_off;
         D.mask_off = mask_off;
         D.item_off = items;
@@ -545,6 +576,7 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
         if ((r = upload_geometry(c, d)) != LBM_OK) { g_create_error = c->msg; return cleanup(r); }
     // rest state in arena 0
     CKCR(launch_fill_rest(c->kind, c->dd, ndom, c->hd.data(), c->f[0], c->solid, c->stream));
+    for (int d = 0; d < ndom; ++d) CKCR(launch_prime_mail(c->kind, c->hd[d], c->f[0], c->nflags, c->stream));
     if (c->np_slots > 0) {
         c->hst.assign(c->np_slots, PartStatic{});
         for (auto& s : c->hst) s.dom = -1;
@@ -597,6 +629,7 @@ int lbm_set_geometry(lbm_ctx* c, int dom, const uint8_t* solid) {
     if (r) return r;
     CKC(c, launch_export(c->kind, D, c->f[c->cur], c->solid, c->d_stage, c->stream));
     CKC(c, launch_import(c->kind, D, c->d_stage, c->f[c->cur], c->solid, c->stream));
+    CKC(c, launch_prime_mail(c->kind, D, c->f[c->cur], c->nflags, c->stream));
     return sync_and_check(c);
 }
 
@@ -690,6 +723,7 @@ int lbm_set_populations(lbm_ctx* c, int dom, const double* f) {
     if (r) return r;
     CKC(c, cudaMemcpyAsync(c->d_stage, f, bytes, cudaMemcpyHostToDevice, c->stream));
     CKC(c, launch_import(c->kind, D, c->d_stage, c->f[c->cur], c->solid, c->stream));
+    CKC(c, launch_prime_mail(c->kind, D, c->f[c->cur], c->nflags, c->stream));
     return sync_and_check(c);
 }
 
@@ -852,7 +886,7 @@ int lbm_save(lbm_ctx* c, const char* path) {
     CkptHeader h;
     memset(&h, 0, sizeof h);
     memcpy(h.magic, "LBMGB300", 8);
-    h.version = 1;
+    h.version = 2;  // 2: planes carry ghost rows with y walls
     h.kind = c->kind;
     h.ndom = c->ndom;
     h.np_slots = c->np_slots;
@@ -901,7 +935,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
     if (!fp) return fail(c, LBM_E_IO, std::string("cannot open ") + path);
     auto bail = [&](const char* m) { fclose(fp); return fail(c, LBM_E_IO, m); };
     CkptHeader h;
-    if (fread(&h, sizeof h, 1, fp) != 1 || memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 1) return bail("not a checkpoint");
+    if (fread(&h, sizeof h, 1, fp) != 1 || memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 2) return bail("not a checkpoint");
     if (h.kind != c->kind || h.ndom != c->ndom || h.np_slots != c->np_slots || h.arena_elems != (int64_t)c->arena_elems)
         return bail("checkpoint does not match this context");
     std::vector<lbm_params> prm(c->ndom);
@@ -1032,36 +1066,66 @@ int lbm_autotune(lbm_ctx* c, int trial_steps) {
     if (r) return r;
     // Trials write only the scratch arena f[cur^1] and its step counter, both
     // of which the next real step overwrites; the state f[cur] is read-only.
-    const int blocks[] = {128, 256, 512};
+    struct Cand { int mode, block, stages; };
+    std::vector<Cand> cands;
+    for (int mode = 0; mode < 2; ++mode)
+        for (int b : {128, 256, 512}) cands.push_back({mode, b, 0});
+    for (Cand k : {Cand{2, 32, 1}, Cand{2, 64, 1}, Cand{2, 64, 2}, Cand{2, 128, 1}, Cand{2, 128, 2}, Cand{2, 256, 1}})
+        if (staged_blocks_per_sm(c->kind, c->noise, c->pl, k.block, k.stages) > 0) cands.push_back(k);
     cudaEvent_t e0, e1;
     CKC(c, cudaEventCreate(&e0));
     CKC(c, cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_block = c->block, best_mode = c->grid_mode;
-    {
-        for (int mode = 0; mode < 2; ++mode)
-            for (int b : blocks) {
-                c->block = b;
-                c->grid_mode = mode;
-                set_launch(c);
-                cudaError_t e = enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid);
-                if (e != cudaSuccess) continue;
-                cudaEventRecord(e0, c->stream);
-                for (int s = 0; s < trial_steps && e == cudaSuccess; ++s)
-                    e = enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid);
-                cudaEventRecord(e1, c->stream);
-                if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) continue;
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) { best = ms; best_block = b; best_mode = mode; }
-            }
+    Cand keep{c->grid_mode, c->block, c->stages};
+    for (const Cand& k : cands) {
+        c->grid_mode = k.mode;
+        c->block = k.block;
+        c->stages = k.stages;
+        set_launch(c);
+        cudaError_t e = enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid);
+        if (e != cudaSuccess) continue;
+        cudaEventRecord(e0, c->stream);
+        for (int s = 0; s < trial_steps && e == cudaSuccess; ++s)
+            e = enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid);
+        cudaEventRecord(e1, c->stream);
+        if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) continue;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; keep = k; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->block = best_block;
-    c->grid_mode = best_mode;
+    c->grid_mode = keep.mode;
+    c->block = keep.block;
+    c->stages = keep.stages;
     set_launch(c);
     return sync_and_check(c);
+}
+
+int lbm_set_launch(lbm_ctx* c, int32_t kernel, int32_t block, int32_t stages) {
+    if (!c) return LBM_E_INVAL;
+    if (kernel < 0 || kernel > 2 || block < 32 || block > 512 || block % 32 != 0)
+        return fail(c, LBM_E_INVAL, "kernel must be 0..2 and block a multiple of 32 in [32, 512]");
+    if (kernel == 2) {
+        if (stages < 1 || stages > STAGED_MAX_STAGES || block > STAGED_MAX_BLOCK)
+            return fail(c, LBM_E_INVAL, "staged kernel: stages 1..8 and block <= 256");
+        if (staged_blocks_per_sm(c->kind, c->noise, c->pl, block, stages) < 1)
+            return fail(c, LBM_E_INVAL, "staged kernel: the shared memory of one CTA does not fit an SM");
+    }
+    c->grid_mode = kernel;
+    c->block = block;
+    c->stages = kernel == 2 ? stages : 0;
+    set_launch(c);
+    return LBM_OK;
+}
+
+int lbm_get_launch(const lbm_ctx* c, int64_t* out4) {
+    if (!c || !out4) return LBM_E_INVAL;
+    out4[0] = c->grid_mode;
+    out4[1] = c->block;
+    out4[2] = c->stages;
+    out4[3] = c->grid;
+    return LBM_OK;
 }
 
 }  // extern "C"

@@ -33,6 +33,35 @@ __global__ void k_fill_rest(DomDev D, typename S::T* arena, const uint8_t* solid
     }
 }
 
+// Mailbox bounce-back set-up: every fluid node with flag bit j copies its
+// stored slot j into slot opp(j) of its solid or ghost-row neighbour x + e_j,
+// as the stream-collide step does after each collision.  On a state the
+// step produced this rewrites equal values.
+template <class S>
+__global__ void k_prime_mail(DomDev D, typename S::T* arena, const uint16_t* nflags) {
+    const int64_t n = (int64_t)D.nx * D.ny;
+    typename S::T* base = arena + D.off;
+    const bool py = D.flags & FLAG_PY;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(k / D.nx), x = (int)(k - (int64_t)y * D.nx);
+        const int64_t ni = (int64_t)y * D.pitch + x;
+        const uint32_t fl = nflags[D.node_off + ni];
+        if ((fl & NF_SOLID) || !(fl & 0x1FEu)) continue;
+#pragma unroll
+        for (int j = 1; j < 9; ++j) {
+            if (!(fl & (1u << j))) continue;
+            int tx = x + cx(j), ty = y + cy(j);
+            if (tx < 0) tx += D.nx;
+            if (tx >= D.nx) tx -= D.nx;
+            if (py) {
+                if (ty < 0) ty += D.ny;
+                if (ty >= D.ny) ty -= D.ny;
+            }
+            base[(int64_t)opp(j) * D.plane + (int64_t)ty * D.pitch + tx] = base[(int64_t)j * D.plane + ni];
+        }
+    }
+}
+
 template <class S>
 __global__ void k_import(DomDev D, const double* in, typename S::T* arena, const uint8_t* solid) {
     const int64_t n = (int64_t)D.nx * D.ny;
@@ -148,6 +177,12 @@ cudaError_t launch_fill_rest(int kind, const DomDev*, int ndom, const DomDev* hd
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_prime_mail(int kind, const DomDev& D, void* arena, const uint16_t* nflags, cudaStream_t s) {
+    const int64_t nb = blocks_for((int64_t)D.nx * D.ny, 256);
+    LBM_DISPATCH(kind, (k_prime_mail<S><<<(unsigned)nb, 256, 0, s>>>(D, static_cast<S::T*>(arena), nflags)));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_import(int kind, const DomDev& D, const double* in, void* arena, const uint8_t* solid,

@@ -37,14 +37,27 @@ struct StreamArgs {
 };
 enum { STREAM_ALL = 0, STREAM_FAR = 1, STREAM_NEAR = 2 };
 
+// stages == 0: the register-pipelined kernel (every mode).  stages >= 1 with
+// mode ALL or FAR: the staged kernel, in which each warp keeps `stages` row
+// segments in flight through bulk asynchronous copies into shared memory;
+// mode NEAR always takes the register kernel.
 cudaError_t launch_stream_collide(int kind, bool noise, bool pl, const StreamArgs& a, int block, int64_t grid,
-                                  cudaStream_t s);
+                                  int stages, cudaStream_t s);
 int store_vector_width(int kind);
+// Dynamic shared memory of one CTA of the staged kernel, and how many such
+// CTAs fit on one SM (0 when none does or the arguments are out of range).
+size_t staged_smem_bytes(int kind, int block, int stages);
+int staged_blocks_per_sm(int kind, bool noise, bool pl, int block, int stages);
+constexpr int STAGED_MAX_STAGES = 8;
+constexpr int STAGED_MAX_BLOCK = 256;
 
 // ---- auxiliary kernels (k_aux.cu) ----
 // Rest state f* = omega_i rho0 on every fluid node of every domain.
 cudaError_t launch_fill_rest(int kind, const DomDev* doms, int ndom, const DomDev* hdoms, void* arena,
                              const uint8_t* solid, cudaStream_t s);
+// Mailbox bounce-back slots of one domain from its stored fluid populations
+// (after any write of the populations other than a step).
+cudaError_t launch_prime_mail(int kind, const DomDev& D, void* arena, const uint16_t* nflags, cudaStream_t s);
 // Host-order FP64 f[9][ny][nx] (device buffer) -> stored populations of one domain.
 cudaError_t launch_import(int kind, const DomDev& D, const double* in, void* arena, const uint8_t* solid,
                           cudaStream_t s);

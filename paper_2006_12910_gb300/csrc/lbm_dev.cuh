@@ -154,38 +154,64 @@ __device__ __forceinline__ void thetas(uint32_t node, uint32_t step, uint32_t do
 }
 
 // ---------------------------------------------------------------------------
-// Per-domain parameters in the arithmetic type, loaded once per work item so
-// the collision never converts between FP64 and FP32.
+// Per-domain parameters in the arithmetic type (no FP64 <-> FP32 conversion in
+// the collision).  HotPrm (lbm_types.h) holds what every node needs and is
+// read with 16-byte loads; ExtPrm holds what only the power-law, noise or
+// Zou-He nodes need and is read only by those variants.
 // ---------------------------------------------------------------------------
+template <typename A> __device__ __forceinline__ HotPrm<A> load_hot(const DomDev& D);
+template <> __device__ __forceinline__ HotPrm<float> load_hot<float>(const DomDev& D) {
+    const float4* p = reinterpret_cast<const float4*>(&D.hot_f);
+    const float4 a = __ldg(p), b = __ldg(p + 1);
+    HotPrm<float> H;
+    H.omega = a.x; H.om = a.y; H.tgx = a.z; H.tgy = a.w;
+    H.rho0 = b.x; H.scale = b.y; H.inv_scale = b.z; H.pad = b.w;
+    return H;
+}
+template <> __device__ __forceinline__ HotPrm<double> load_hot<double>(const DomDev& D) {
+    const double2* p = reinterpret_cast<const double2*>(&D.hot_d);
+    const double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+    HotPrm<double> H;
+    H.omega = a.x; H.om = a.y; H.tgx = b.x; H.tgy = b.y;
+    H.rho0 = c.x; H.scale = c.y; H.inv_scale = d.x; H.pad = d.y;
+    return H;
+}
+
 template <typename A>
-struct Prm {
-    A tau, inv_tau, rho0, gx, gy, kT, n, xi, tmin, tmax, tmin_pow, tmax_pow;
-    A rho_in, rho_out, d_in, d_out, scale, inv_scale;
+struct ExtPrm {
+    A gx, gy, kT, xi, n, tmin, tmax, tmin_pow, tmax_pow;
     int n_is_one;
     uint32_t dom_id;
     uint64_t seed;
 };
-template <typename A> __device__ __forceinline__ Prm<A> load_prm(const DomDev& D);
-template <> __device__ __forceinline__ Prm<float> load_prm<float>(const DomDev& D) {
-    Prm<float> P;
-    P.tau = D.tau_f; P.inv_tau = D.inv_tau_f; P.rho0 = D.rho0_f; P.gx = D.gx_f; P.gy = D.gy_f; P.kT = D.kT_f;
-    P.n = D.n_pl_f; P.xi = D.xi_pl_f; P.tmin = D.tau_min_f; P.tmax = D.tau_max_f;
-    P.tmin_pow = D.tmin_pow_f; P.tmax_pow = D.tmax_pow_f;
-    P.rho_in = D.rho_in_f; P.rho_out = D.rho_out_f; P.d_in = D.drho_in_f; P.d_out = D.drho_out_f;
-    P.scale = D.scale_f; P.inv_scale = D.inv_scale_f;
-    P.n_is_one = D.n_is_one; P.dom_id = D.domain_id; P.seed = D.seed;
-    return P;
+template <typename A, bool NOISE, bool PL>
+__device__ __forceinline__ ExtPrm<A> load_ext(const DomDev& D) {
+    ExtPrm<A> X{};
+    const bool f = sizeof(A) == 4;
+    if (PL) {
+        X.gx = (A)(f ? D.gx_f : D.gx); X.gy = (A)(f ? D.gy_f : D.gy);
+        X.xi = (A)(f ? D.xi_pl_f : D.xi_pl); X.n = (A)(f ? D.n_pl_f : D.n_pl);
+        X.tmin = (A)(f ? D.tau_min_f : D.tau_min); X.tmax = (A)(f ? D.tau_max_f : D.tau_max);
+        X.tmin_pow = (A)(f ? D.tmin_pow_f : D.tmin_pow); X.tmax_pow = (A)(f ? D.tmax_pow_f : D.tmax_pow);
+        X.n_is_one = D.n_is_one;
+    }
+    if (NOISE) {
+        X.kT = (A)(f ? D.kT_f : D.kT);
+        X.dom_id = D.domain_id;
+        X.seed = D.seed;
+    }
+    return X;
 }
-template <> __device__ __forceinline__ Prm<double> load_prm<double>(const DomDev& D) {
-    Prm<double> P;
-    P.tau = D.tau; P.inv_tau = D.inv_tau; P.rho0 = D.rho0; P.gx = D.gx; P.gy = D.gy; P.kT = D.kT;
-    P.n = D.n_pl; P.xi = D.xi_pl; P.tmin = D.tau_min; P.tmax = D.tau_max;
-    P.tmin_pow = D.tmin_pow; P.tmax_pow = D.tmax_pow;
-    P.rho_in = D.rho_in; P.rho_out = D.rho_out; P.d_in = D.drho_in; P.d_out = D.drho_out;
-    P.scale = D.scale; P.inv_scale = D.inv_scale;
-    P.n_is_one = D.n_is_one; P.dom_id = D.domain_id; P.seed = D.seed;
-    return P;
+
+// Reciprocal of the density: FP32 takes the hardware approximation (relative
+// error below 2^-22, far inside the FP32 path's tolerance); FP64 divides.
+template <typename A> __device__ __forceinline__ A rcp_rho(A r);
+template <> __device__ __forceinline__ float rcp_rho<float>(float r) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r));
+    return y;
 }
+template <> __device__ __forceinline__ double rcp_rho<double>(double r) { return 1.0 / r; }
 
 // ---------------------------------------------------------------------------
 // Power-law relaxation time, Sec. 5.  The shear rate of Eq. nn2 with Pi_D of
@@ -200,7 +226,7 @@ template <> __device__ __forceinline__ float powa<float>(float x, float e) { ret
 template <> __device__ __forceinline__ double powa<double>(double x, double e) { return exp2(e * log2(x)); }
 
 template <typename A>
-__device__ __forceinline__ A solve_tau_pl(A Astr, const Prm<A>& P) {
+__device__ __forceinline__ A solve_tau_pl(A Astr, const ExtPrm<A>& P) {
     const A n = P.n, tmin = P.tmin, tmax = P.tmax;
     if (P.n_is_one) {
         A t = (A)0.5 + (A)3.0 * P.xi;
@@ -232,49 +258,77 @@ __device__ __forceinline__ A solve_tau_pl(A Astr, const Prm<A>& P) {
 // rho u = sum f e + tau rho g, optional tau* of Eq. nn5 and noise of NP1-NP2).
 // f holds the pre-collision populations, shifted by omega_i rho0 when SHIFT;
 // on return it holds the post-collision values in the same units.
+// Arranged for few operations, with omega = 1/tau and
+// p_i = 3 e.u + 9/2 (e.u)^2 - 3/2 u.u; the pair (i, opp(i)) shares
+// 9/2 (e.u)^2 - 3/2 u.u and 3 e.u.  Shifted stores (values f - w_i rho0, of
+// the size of the non-equilibrium part) relax as
+//   f_i' = (1 - omega) f_i + w_i (B + R p_i),  R = omega rho, B = omega (rho - rho0);
+// unshifted stores (values ~ w_i) keep the difference form
+//   f_i' = f_i + omega (w_i rho (1 + p_i) - f_i),
+// whose rounding error stays at the scale of f_i rather than of omega f_i.
 // Returns false when rho is not a positive finite number.
 // ---------------------------------------------------------------------------
+template <typename A, bool SHIFT>
+__device__ __forceinline__ void relax_pair(A& fi, A& fo, A e, A w, A usq, A R, A R3, A B, A om, A omega) {
+    const A q = (A)4.5 * e * e - usq;
+    if (SHIFT) {
+        const A h = B + R * q;
+        const A k = R3 * e;
+        fi = om * fi + w * (h + k);
+        fo = om * fo + w * (h - k);
+    } else {  // here R = rho, R3 = 3 rho, B = rho
+        const A h = B + R * q;
+        const A k = R3 * e;
+        fi = fi + omega * (w * (h + k) - fi);
+        fo = fo + omega * (w * (h - k) - fo);
+    }
+}
+
 template <typename A, bool SHIFT, bool NOISE, bool PL>
-__device__ __forceinline__ bool collide_node(A f[9], const Prm<A>& P, uint32_t node, uint32_t step) {
-    A s = f[0];
-#pragma unroll
-    for (int i = 1; i < 9; ++i) s += f[i];
-    const A jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    const A jy = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
-    const A rho0 = P.rho0;
-    const A rho = SHIFT ? rho0 + s : s;
-    const A drho = SHIFT ? s : s - rho0;
+__device__ __forceinline__ bool collide_node(A f[9], const HotPrm<A>& H, const ExtPrm<A>& X, uint32_t node,
+                                             uint32_t step) {
+    const A a = (f[1] + f[5]) + f[8];  // e_x > 0
+    const A b = (f[3] + f[6]) + f[7];  // e_x < 0
+    const A c = (f[2] + f[5]) + f[6];  // e_y > 0
+    const A d = (f[4] + f[7]) + f[8];  // e_y < 0
+    const A s = (f[0] + (f[2] + f[4])) + (a + b);
+    const A jx = a - b, jy = c - d;
+    const A rho = SHIFT ? H.rho0 + s : s;
+    const A drho = SHIFT ? s : s - H.rho0;
     const bool ok = (rho > (A)0) && (rho < (A)1e30);
-    const A irho = (A)1 / rho;
-    A tau = P.tau, itau = P.inv_tau;
+    const A irho = rcp_rho<A>(rho);
+    A omega = H.omega, om = H.om, tgx = H.tgx, tgy = H.tgy;
     if (PL) {
-        const A sxx = (f[1] + f[3]) + (f[5] + f[6]) + (f[7] + f[8]);
-        const A syy = (f[2] + f[4]) + (f[5] + f[6]) + (f[7] + f[8]);
-        const A sxy = (f[5] - f[6]) + (f[7] - f[8]);
+        const A sxy = (f[5] + f[7]) - (f[6] + f[8]);
         const A iso = SHIFT ? drho * (A)(1.0 / 3.0) : rho * (A)(1.0 / 3.0);
-        const A pxx = sxx - iso - jx * jx * irho;
-        const A pyy = syy - iso - jy * jy * irho;
+        const A pxx = (a + b) - iso - jx * jx * irho;
+        const A pyy = (c + d) - iso - jy * jy * irho;
         const A pxy = sxy - jx * jy * irho;
         const A det = pxy * pxy - pxx * pyy;
         const A Astr = (A)3 * sqrt(fabs(det)) * irho;
-        tau = solve_tau_pl<A>(Astr, P);
-        itau = (A)1 / tau;
+        const A tau = solve_tau_pl<A>(Astr, X);
+        omega = (A)1 / tau;
+        om = (A)1 - omega;
+        tgx = tau * X.gx;
+        tgy = tau * X.gy;
     }
-    const A ux = (jx + tau * rho * P.gx) * irho;
-    const A uy = (jy + tau * rho * P.gy) * irho;
+    const A ux = (jx + rho * tgx) * irho;
+    const A uy = (jy + rho * tgy) * irho;
     const A usq = (A)1.5 * (ux * ux + uy * uy);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const A eu = (A)cx(i) * ux + (A)cy(i) * uy;
-        const A poly = (A)3 * eu + (A)4.5 * eu * eu - usq;
-        const A feq = SHIFT ? (A)wgt(i) * (drho + rho * poly) : (A)wgt(i) * rho * ((A)1 + poly);
-        f[i] = f[i] + (feq - f[i]) * itau;
-    }
+    const A R = SHIFT ? omega * rho : rho;
+    const A B = SHIFT ? omega * drho : rho;
+    const A R3 = (A)3 * R;
+    if (SHIFT) f[0] = om * f[0] + (A)wgt(0) * (B - R * usq);
+    else f[0] = f[0] + omega * ((A)wgt(0) * (B - R * usq) - f[0]);
+    relax_pair<A, SHIFT>(f[1], f[3], ux, (A)wgt(1), usq, R, R3, B, om, omega);
+    relax_pair<A, SHIFT>(f[2], f[4], uy, (A)wgt(2), usq, R, R3, B, om, omega);
+    relax_pair<A, SHIFT>(f[5], f[7], ux + uy, (A)wgt(5), usq, R, R3, B, om, omega);
+    relax_pair<A, SHIFT>(f[6], f[8], uy - ux, (A)wgt(6), usq, R, R3, B, om, omega);
     if (NOISE) {
-        if (P.kT > (A)0) {
+        if (X.kT > (A)0) {
             A th[6];
-            thetas<A>(node, step, P.dom_id, P.seed, th);
-            const A amp = sqrt(rho * P.kT * itau * ((A)2 - itau) * (A)3);
+            thetas<A>(node, step, X.dom_id, X.seed, th);
+            const A amp = sqrt(rho * X.kT * omega * ((A)2 - omega) * (A)3);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 A z = (A)0;
@@ -290,11 +344,16 @@ __device__ __forceinline__ bool collide_node(A f[9], const Prm<A>& P, uint32_t n
 
 // Zou-He density column (Zou & He 1997).  side 0: inlet at x = 0, the
 // populations 1, 5, 8 enter from outside; side 1: outlet at x = nx-1, the
-// populations 3, 6, 7 enter.  rho_b is the prescribed density and d_b its
-// excess over the rest density of the stored values (rho_b - rho0 when SHIFT,
-// rho_b otherwise); the shifts of the paired populations are equal.
+// populations 3, 6, 7 enter.  d_b is the prescribed density in the units of
+// the stored values (rho_b - rho0 when SHIFT, rho_b otherwise); the shifts of
+// the paired populations are equal.
 template <typename A>
-__device__ __forceinline__ void zou_he(A f[9], int side, A rho_b, A d_b) {
+__device__ __forceinline__ A zou_he_excess(const DomDev& D, int side) {
+    if (sizeof(A) == 4) return (A)(side == 0 ? D.drho_in_f : D.drho_out_f);
+    return (A)(side == 0 ? D.drho_in : D.drho_out);
+}
+template <typename A>
+__device__ __forceinline__ void zou_he(A f[9], int side, A d_b) {
     if (side == 0) {
         const A ru = d_b - (f[0] + f[2] + f[4] + (A)2 * (f[3] + f[6] + f[7]));
         f[1] = f[3] + (A)(2.0 / 3.0) * ru;
@@ -306,7 +365,6 @@ __device__ __forceinline__ void zou_he(A f[9], int side, A rho_b, A d_b) {
         f[7] = f[5] + (A)0.5 * (f[2] - f[4]) - (A)(1.0 / 6.0) * ru;
         f[6] = f[8] - (A)0.5 * (f[2] - f[4]) - (A)(1.0 / 6.0) * ru;
     }
-    (void)rho_b;
 }
 
 }  // namespace lbmk

@@ -18,12 +18,25 @@ enum : uint32_t {
     ERR_TIMEOUT = 4u,   // a bounded device wait ran out
 };
 
+// Collision parameters read by every stream-collide work item, packed for
+// 16-byte loads: omega = 1/tau, om = 1 - omega, tgx/tgy = tau g (the
+// velocity shift of the forcing), rho0, and the store scale and its inverse.
+template <typename A>
+struct alignas(16) HotPrm {
+    A omega, om, tgx, tgy, rho0, scale, inv_scale, pad;
+};
+
 // One lattice domain as the kernels see it.  Populations of plane i live at
-// arena[off + i*plane + y*pitch + x]; per-node solid bytes and flag words at
-// nodes[node_off + y*pitch + x];
-// the special-chunk bitmask word of warp segment s of row y at
-// special[mask_off + y*seg_per_row + s] (bit = lane; a chunk is V nodes).
-struct DomDev {
+// arena[off + i*plane + y*pitch + x]; with y walls each plane also holds one
+// ghost row on each side (y = -1 and y = ny, still addressed as off + i*plane
+// + y*pitch + x), whose slots carry the bounced-back populations of the wall
+// rows.  Per-node solid bytes, flag words and tags at
+// nodes[node_off + y*pitch + x], 0 <= y < ny; the special-chunk bitmask word of
+// warp segment s of row y at special[mask_off + y*seg_per_row + s] (bit =
+// lane; a chunk is V nodes).
+struct alignas(16) DomDev {
+    HotPrm<double> hot_d;
+    HotPrm<float> hot_f;
     int32_t nx, ny, pitch, flags;
     int64_t off, plane, node_off, mask_off, item_off;
     int32_t seg_per_row, V;
@@ -42,14 +55,21 @@ struct DomDev {
     float n_pl_f, xi_pl_f, tau_min_f, tau_max_f, tmin_pow_f, tmax_pow_f, scale_f, inv_scale_f;
 };
 
-// Per-node flag bits (uint16), written from the geometry on the host.  Bit i
-// (1..8): direction i is bounced back (its pull source is solid, beyond a
-// wall, or outside the x range at a wall-corner node).  A chunk whose nodes
-// all have zero flags takes the plain vector path without reading them.
+// Per-node flag words (uint16), written from the geometry on the host.
+// Halfway bounce-back uses the slots of solid nodes and wall ghost rows as
+// mailboxes: a fluid node whose neighbour x + e_j is solid or a ghost-row
+// node carries bit j (1..8), and after its collision it writes its outgoing
+// f*_j into slot opp(j) of that neighbour, the slot it pulls direction opp(j)
+// from in the next step.  Pulls therefore need no patching, except at the
+// wall-corner nodes of open ends (NF_CORNER: the directions whose source lies
+// beyond the x range take the node's own opposite slot) and on the Zou-He
+// columns.  A chunk whose nodes all have zero flags takes the plain vector
+// path without reading them.
 enum : uint16_t {
     NF_SOLID = 1u << 0,
     NF_ZH_IN = 1u << 9,    // Zou-He inlet node (x = 0)
     NF_ZH_OUT = 1u << 10,  // Zou-He outlet node (x = nx - 1)
+    NF_CORNER = 1u << 11,  // wall-corner node of an open end
 };
 
 // Particle data on the device (Sec. 3).  State is double precision.

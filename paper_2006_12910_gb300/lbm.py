@@ -25,8 +25,8 @@ EXPORTED = [
     "lbm_create", "lbm_create_ensemble", "lbm_set_geometry", "lbm_add_particles", "lbm_set_populations",
     "lbm_get_populations", "lbm_step", "lbm_sync", "lbm_moments", "lbm_moments_device", "lbm_moments_async",
     "lbm_moments_async_wait", "lbm_particles", "lbm_particle_forces", "lbm_checks", "lbm_step_count",
-    "lbm_save", "lbm_load", "lbm_autotune", "lbm_profile_steps", "lbm_checks_noalloc", "lbm_last_error",
-    "lbm_destroy",
+    "lbm_save", "lbm_load", "lbm_autotune", "lbm_set_launch", "lbm_get_launch", "lbm_profile_steps",
+    "lbm_checks_noalloc", "lbm_last_error", "lbm_destroy",
 ]
 NOALLOC_MAX_ROWS = 16384
 
@@ -104,6 +104,8 @@ def load(build_if_missing: bool = True):
             "lbm_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
             "lbm_load": (ctypes.c_int, [_vp, ctypes.c_char_p]),
             "lbm_autotune": (ctypes.c_int, [_vp, ctypes.c_int]),
+            "lbm_set_launch": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+            "lbm_get_launch": (ctypes.c_int, [_vp, _P(ctypes.c_int64)]),
             "lbm_profile_steps": (ctypes.c_int, [_vp, ctypes.c_int64, _dp, _P(ctypes.c_int64)]),
             "lbm_checks_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                   ctypes.c_int32, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp]),
@@ -278,6 +280,16 @@ class Context:
 
     def autotune(self, trial_steps=20):
         self._ck(self.L.lbm_autotune(self.h, int(trial_steps)))
+
+    def set_launch(self, kernel, block, stages=0):
+        """Stream-collide kernel (0 register, 1 register persistent, 2 staged), threads per block, stages."""
+        self._ck(self.L.lbm_set_launch(self.h, int(kernel), int(block), int(stages)))
+
+    def launch(self):
+        """(kernel, block, stages, grid) of the stream-collide launches."""
+        out = (ctypes.c_int64 * 4)()
+        self._ck(self.L.lbm_get_launch(self.h, out))
+        return tuple(int(v) for v in out)
 
 
 def checks_noalloc(d_populations, store, nx, ny, pitch, rho0, store_scale, d_solid, d_out3, stream=None):

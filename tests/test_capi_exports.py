@@ -44,3 +44,5 @@ def test_invalid_parameters_rejected_without_gpu():
         assert L.lbm_last_error(None)
     assert L.lbm_step(None, 1) == -1
     assert L.lbm_step_count(None) == -1
+    assert L.lbm_set_launch(None, 2, 128, 2) == -1
+    assert L.lbm_get_launch(None, None) == -1
