@@ -296,6 +296,7 @@ void set_launch(lbm_ctx* c) {
 PartArgs part_args(lbm_ctx* c, int cur) {
     PartArgs a;
     a.doms = c->dd;
+    a.one_domain = c->ndom == 1;
     a.arena = c->f[cur];
     a.solid = c->solid;
     a.state = c->pstate;

@@ -1,10 +1,11 @@
 // k_part.cu -- particle kernel of the D2Q9 hot path (arXiv:2006.12910 Sec. 3).
 //
-// One launch per timestep with two CTAs per particle that run side by side
-// (roles A and B below).  The stored populations are f*(t), post-collision;
-// the particle state and the link / flip lists are double-buffered by the
-// parity of the step, so A reads the lists of t while B writes those of t+1.
-// Role A (phases 1-2) and role B (phase 3):
+// One launch per timestep with three CTAs per particle that run side by side
+// (roles A, B and C below).  The stored populations are f*(t),
+// post-collision; the particle state and the link / flip lists are
+// double-buffered by the parity of the step, so A reads the lists of t while
+// B writes those of t+1.  Role A (phases 1-2), role B (phase 3) and role C
+// (phase 4):
 //  1. forces at t: Eq. MP1 over the boundary links of the rasterisation at t
 //     (each link's slots belong to this particle alone), the covered /
 //     uncovered-node force of Eq. MP3 from the node moments that the
@@ -17,9 +18,9 @@
 //     f*_k(r_v) minus the same, so the plain pull stream realises the moving
 //     bounce-back on both sides;
 //  3. re-rasterisation at r_c(t+1) = r_c(t) + U_p(t), which needs no force and
-//     therefore no other CTA's result: new link list, the nodes that change
-//     side (tagged for the next stream-collide pass), and the work items near
-//     the particle for the next step.
+//     therefore no other CTA's result: new link list and the nodes that change
+//     side (tagged for the next stream-collide pass);
+//  4. the work items near the particle for the next step.
 #include "kernels.h"
 #include "lbm_dev.cuh"
 
@@ -42,23 +43,26 @@ __device__ __forceinline__ bool inside_disk(const DomDev& D, double px, double p
     return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) < __dmul_rn(R, R);
 }
 
-__device__ __forceinline__ bool is_surface(const DomDev& D, double px, double py, double R, int x, int y) {
+__device__ __noinline__ bool is_surface(const DomDev& D, double px, double py, double R, int x, int y) {
     if (!inside_disk(D, px, py, R, x, y)) return false;
-#pragma unroll
+#pragma unroll 1
     for (int i = 1; i < 9; ++i)
         if (!inside_disk(D, px, py, R, x + cx(i), y + cy(i))) return true;
     return false;
 }
 
-// Wrap a node into the domain; false when it leaves through a non-periodic edge.
+// Wrap a node into the domain; false when it leaves through a non-periodic
+// edge.  Nodes handled here lie within R + 8 of the domain, and a particle
+// on a periodic axis has 2R + 8 below the period, so one period step (no
+// division) brings them in.
 __device__ __forceinline__ bool wrap_node(const DomDev& D, int& x, int& y) {
     if (x < 0 || x >= D.nx) {
         if (!(D.flags & FLAG_PX)) return false;
-        x = ((x % D.nx) + D.nx) % D.nx;
+        x += x < 0 ? D.nx : -D.nx;
     }
     if (y < 0 || y >= D.ny) {
         if (!(D.flags & FLAG_PY)) return false;
-        y = ((y % D.ny) + D.ny) % D.ny;
+        y += y < 0 ? D.ny : -D.ny;
     }
     return true;
 }
@@ -87,7 +91,7 @@ struct DiskF {
     int cx, cy;
     float fx, fy, R2, margin;
 };
-__device__ __forceinline__ DiskF make_diskf(double px, double py, double R) {
+__device__ __noinline__ DiskF make_diskf(double px, double py, double R) {
     DiskF d;
     d.px = px; d.py = py; d.R = R;
     d.cx = (int)floor(px); d.cy = (int)floor(py);
@@ -96,13 +100,30 @@ __device__ __forceinline__ DiskF make_diskf(double px, double py, double R) {
     d.margin = 1e-3f * fmaxf(1.0f, d.R2 * 0.01f) + 1e-4f;
     return d;
 }
-// Integer minimum image of a node offset along a periodic axis.
+// Integer minimum image, in [-L/2, L/2), of a node offset along a periodic
+// axis.  Offsets here (a node within R + 8 of the domain against a centre in
+// it, with 2R + 8 below the period) are under 5L/2 in magnitude, so two
+// period steps (no division) suffice.
 __device__ __forceinline__ int wrap_off(int d, int L, bool periodic) {
     if (!periodic) return d;
-    d %= L;
-    if (d < 0) d += L;
-    if (2 * d >= L) d -= L;
+    if (2 * d >= L) {
+        d -= L;
+        if (2 * d >= L) d -= L;
+    } else if (2 * d < -L) {
+        d += L;
+        if (2 * d < -L) d += L;
+    }
     return d;
+}
+// The exact FP64 decision near the rim (out of line: rarely taken, and the
+// particle kernel is bound by instruction fetch, so its code is kept small).
+__device__ __noinline__ bool inside_exact(const DomDev& D, const DiskF& k, int xu, int yu, bool wrapped) {
+    if (wrapped) {
+        int x = xu, y = yu;
+        if (!wrap_node(D, x, y)) { x = xu; y = yu; }
+        return inside_disk(D, k.px, k.py, k.R, x, y);
+    }
+    return inside_disk(D, k.px, k.py, k.R, xu, yu);
 }
 __device__ __forceinline__ bool inside_f(const DomDev& D, const DiskF& k, int xu, int yu, bool wrapped) {
     const int dxi = wrap_off(xu - k.cx, D.nx, D.flags & FLAG_PX), dyi = wrap_off(yu - k.cy, D.ny, D.flags & FLAG_PY);
@@ -110,12 +131,7 @@ __device__ __forceinline__ bool inside_f(const DomDev& D, const DiskF& k, int xu
     const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
     if (d2 < k.R2 - k.margin) return true;
     if (d2 > k.R2 + k.margin) return false;
-    if (wrapped) {
-        int x = xu, y = yu;
-        if (!wrap_node(D, x, y)) { x = xu; y = yu; }
-        return inside_disk(D, k.px, k.py, k.R, x, y);
-    }
-    return inside_disk(D, k.px, k.py, k.R, xu, yu);
+    return inside_exact(D, k, xu, yu, wrapped);
 }
 
 template <class S>
@@ -125,7 +141,7 @@ __device__ __forceinline__ double full_pop(const typename S::T* base, const DomD
 }
 
 // Exclusive block scan of small non-negative counts; returns the block total.
-__device__ __forceinline__ int block_scan(int c, int* sh_warp, int& excl) {
+__device__ __noinline__ int block_scan(int c, int* sh_warp, int& excl) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int incl = c;
 #pragma unroll
@@ -145,17 +161,50 @@ __device__ __forceinline__ int block_scan(int c, int* sh_warp, int& excl) {
     return total;
 }
 
+// Warps 3-7 of role A (160 threads) work as one group with their own named
+// barrier, so the other warps of the CTA never wait for them.
+constexpr int LJ_W0 = 3, LJ_NT = 160;
+__device__ __forceinline__ void lj_sync() { asm volatile("bar.sync 1, 160;" ::: "memory"); }
+
+// Exclusive scan of small counts over the LJ group (gt = thread index in the
+// group); returns the group total.  sh holds one int per warp of the group.
+__device__ __noinline__ int lj_scan(int c, int gt, int* sh, int& excl) {
+    const int lane = gt & 31, w = gt >> 5;
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) sh[w] = incl;
+    lj_sync();
+    int wbase = 0, total = 0;
+#pragma unroll
+    for (int k = 0; k < LJ_NT / 32; ++k) {
+        if (k < w) wbase += sh[k];
+        total += sh[k];
+    }
+    excl = wbase + incl - c;
+    lj_sync();
+    return total;
+}
+
+// Fixed-order sum over the lanes of a warp (lane 0 gets the total).
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    return x;
+}
+
 constexpr int PB_CAP = 4096;   // nodes of a shared-memory inside bitmap
 constexpr int MAXNEAR = 64;     // nearby particles considered per particle
 
-// Exclusive block scan of small non-negative counts; returns the block total.
-__device__ __forceinline__ int block_scan(int c, int* sh_warp, int& excl);
 
 // Other particles of the domain whose disks come within `extra` of the disk
 // (x, y, R), in index order, with their FP32 test data.  Every thread tests
 // its share of the particles; a block scan compacts the list, so the order is
 // fixed and no thread walks the particle array alone.
-__device__ __forceinline__ void near_list(const PartArgs& a, const DomDev& D, int p, const PartState* states,
+__device__ __noinline__ void near_list(const PartArgs& a, const DomDev& D, int p, const PartState* states,
                                           double x, double y, double R, double extra, int* list, DiskF* disks,
                                           int* count, int* sh_warp) {
     int total = 0;
@@ -190,58 +239,40 @@ __device__ __forceinline__ void near_list(const PartArgs& a, const DomDev& D, in
 
 // Surface node of a disk (inside, with an 8-neighbour outside), unwrapped
 // coordinates near the disk, using the FP32 test with its exact fallback.
-__device__ __forceinline__ bool is_surface_f(const DomDev& D, const DiskF& k, int x, int y) {
+__device__ __noinline__ bool is_surface_f(const DomDev& D, const DiskF& k, int x, int y) {
     if (!inside_f(D, k, x, y, false)) return false;
-#pragma unroll
+#pragma unroll 1
     for (int i = 1; i < 9; ++i)
         if (!inside_f(D, k, x + cx(i), y + cy(i), false)) return true;
     return false;
 }
 
 // Position at t+1 from the state at t (Sec. 3: r_c(t+1) = r_c(t) + U_p(t)).
+// Periodic wrap c - L floor(c / L); inside [0, L(1 - 1e-9)) the floor is 0,
+// so the FP64 division (slow here) runs only near or beyond the ends, and
+// the result is the same as evaluating the formula everywhere.
+__device__ __forceinline__ double wrap_coord(double c, int L) {
+    if (c >= 0.0 && c < (double)L * (1.0 - 1e-9)) return c;
+    return c - L * floor(c / L);
+}
 __device__ __forceinline__ void next_position(const DomDev& D, const PartState& q, bool fixed, double& x, double& y) {
     if (fixed) { x = q.x; y = q.y; return; }
     x = q.x + q.U;
     y = q.y + q.V;
-    if (D.flags & FLAG_PX) x = x - D.nx * floor(x / D.nx);
-    if (D.flags & FLAG_PY) y = y - D.ny * floor(y / D.ny);
-}
-
-// Fixed-order block sum of the components [c0, c1) of v (deterministic for a
-// fixed blockDim).  FP64 issue rate is low on this part, so the tree first
-// halves across warps in shared memory (4, 2, 1 warps active) and only then
-// shuffles inside warp 0; the totals land in tot[c].
-template <int N>
-__device__ __forceinline__ void block_sum_range(double (&v)[N], int c0, int c1, double* buf, double* tot) {
-    static_assert(PBLOCK == 256, "tree below assumes 256 threads");
-#pragma unroll
-    for (int c = 0; c < N; ++c)
-        if (c >= c0 && c < c1) buf[c * PBLOCK + threadIdx.x] = v[c];
-    __syncthreads();
-    for (int h = PBLOCK / 2; h >= 32; h >>= 1) {
-        if ((int)threadIdx.x < h) {
-#pragma unroll
-            for (int c = 0; c < N; ++c)
-                if (c >= c0 && c < c1) buf[c * PBLOCK + threadIdx.x] += buf[c * PBLOCK + threadIdx.x + h];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x < 32) {
-#pragma unroll
-        for (int c = 0; c < N; ++c) {
-            if (c < c0 || c >= c1) continue;
-            double x = buf[c * PBLOCK + threadIdx.x];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (threadIdx.x == 0) tot[c] = x;
-        }
-    }
-    __syncthreads();
+    if (D.flags & FLAG_PX) x = wrap_coord(x, D.nx);
+    if (D.flags & FLAG_PY) y = wrap_coord(y, D.ny);
 }
 
 // Shared memory of one CTA; role A and role B use disjoint parts of a union.
+constexpr int NB_MAX = 4, NB_W = 32;  // inside bitmaps of up to 4 nearby disks, boxes up to 32 x 32
 struct SmemA {
-    double red[DIAG_N * PBLOCK];
+    double wsum[PBLOCK / 32][DIAG_N];  // per-warp partial sums
+    int16_t surf[LJ_NT];               // surface nodes of one chunk of the box (LJ group)
+    double2 arm[LJ_NT];                // their torque arms
+    int lj_any, lj_ns;
+    int nb_h[NB_MAX];                  // half side of each nearby disk's bitmap (0: none)
+    float nb_lim[MAXNEAR];             // reach of each nearby disk: R + r_it + 2
+    uint8_t nbm[NB_MAX][NB_W * NB_W];  // inside tests of a nearby disk around its centre node
     uint8_t bm[PB_CAP];
     uint8_t wall_win[PB_CAP];
     double lj_fx[LJ_TAB], lj_fy[LJ_TAB];
@@ -249,34 +280,128 @@ struct SmemA {
 };
 struct SmemB {
     uint8_t bnew[PB_CAP], bold[PB_CAP], node_st[PB_CAP];
+    uint16_t res[PB_CAP];  // per box node: link bits 1-8, side change (9), inside the new disk (10)
 };
+
+// What the rasterisation of one particle needs to classify a box node.
+struct RastCtx {
+    const DomDev* D;
+    const uint8_t* solid;
+    const SmemB* sm;
+    const DiskF* near_d;
+    int nn;
+    Box U;
+    bool use_bm, advance;
+    double nxp, nyp, qx, qy, R;
+};
+
+// Inside the disk at t+1 (newdisk) or at t, by the bitmap or the exact test.
+__device__ __noinline__ bool rast_in(const RastCtx& c, bool newdisk, int xu, int yu) {
+    if (c.use_bm) {
+        const int i = (yu - c.U.y0) * c.U.w + (xu - c.U.x0);
+        return (newdisk ? c.sm->bnew[i] : c.sm->bold[i]) != 0;
+    }
+    int x = xu, y = yu;
+    if (!wrap_node(*c.D, x, y)) { x = xu; y = yu; }
+    return newdisk ? inside_disk(*c.D, c.nxp, c.nyp, c.R, x, y) : inside_disk(*c.D, c.qx, c.qy, c.R, x, y);
+}
+
+// Node i of the box U (lattice order): its links (bit k: r_v + e_k outside
+// every disk and not solid), whether it changes side between t and t+1
+// (bit 9) and whether it is inside the disk at t+1 (bit 10); node = its
+// index in the domain.  ovl is set when it lies inside another disk too.
+__device__ __noinline__ uint32_t node_info(const RastCtx& c, int i, int& node, bool& ovl) {
+    const DomDev& D = *c.D;
+    node = 0;
+    const int xu = c.U.x0 + i % c.U.w, yu = c.U.y0 + i / c.U.w;
+    int x = xu, y = yu;
+    if (!wrap_node(D, x, y)) return 0u;
+    node = y * D.pitch + x;
+    const bool solid_here = c.use_bm ? c.sm->node_st[i] == 1 : c.solid[D.node_off + node] != 0;
+    const bool now = rast_in(c, true, xu, yu);
+    uint32_t r = now ? (1u << 10) : 0u;
+    if (now) {
+#pragma unroll 1
+        for (int j = 0; j < c.nn; ++j)
+            if (inside_f(D, c.near_d[j], xu, yu, true)) ovl = true;
+        if (!solid_here) {
+#pragma unroll 1
+            for (int k = 1; k < 9; ++k) {
+                const int fxu = xu + cx(k), fyu = yu + cy(k);
+                if (c.use_bm) {
+                    if (c.sm->node_st[(fyu - c.U.y0) * c.U.w + (fxu - c.U.x0)] != 0) continue;
+                } else {
+                    int fx = fxu, fy = fyu;
+                    if (!wrap_node(D, fx, fy)) continue;
+                    if (c.solid[D.node_off + (int64_t)fy * D.pitch + fx]) continue;
+                }
+                bool in_any = rast_in(c, true, fxu, fyu);
+#pragma unroll 1
+                for (int j = 0; j < c.nn && !in_any; ++j) in_any = inside_f(D, c.near_d[j], fxu, fyu, true);
+                if (!in_any) r |= 1u << k;
+            }
+        }
+    }
+    if (c.advance && !solid_here && now != rast_in(c, false, xu, yu)) r |= 1u << 9;
+    return r;
+}
 union SmemU {
     SmemA A;
     SmemB B;
 };
 
+// Status of every node of the box Bx, by nt threads (t = this thread's
+// index among them): 0 fluid, 1 solid, 2 beyond an open end, 3 beyond a y
+// wall.  Eight loads per thread are issued before any is used, so the solid
+// bytes arrive in one round trip instead of one per node.
+__device__ __forceinline__ void box_status(const DomDev& D, const uint8_t* solid, const Box& Bx, uint8_t* out, int t,
+                                           int nt) {
+    const int n = Bx.n();
+#pragma unroll 1
+    for (int base = 0; base < n; base += 8 * nt) {
+        uint8_t v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = base + u * nt + t;
+            v[u] = 2;
+            if (i < n) {
+                int x = Bx.x0 + i % Bx.w, y = Bx.y0 + i / Bx.w;
+                const bool ywall = (D.flags & FLAG_WY) && (y < 0 || y >= D.ny);
+                if (wrap_node(D, x, y)) v[u] = __ldg(solid + D.node_off + (int64_t)y * D.pitch + x) ? 1 : 0;
+                else v[u] = ywall ? 3 : 2;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = base + u * nt + t;
+            if (i < n) out[i] = v[u];
+        }
+    }
+}
+
 template <class S>
 __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes) {
     typedef typename S::A A;
-    const bool role_b = (int)blockIdx.x >= a.np;
-    const int p = role_b ? blockIdx.x - a.np : blockIdx.x;
+    const int role = (int)blockIdx.x / a.np;  // 0: forces and exchange, 1: rasterisation, 2: near-item marks
+    const int p = (int)blockIdx.x - role * a.np;
+    // Independent loads first (step counter, static data, both parities of
+    // the state), so the prologue waits for one round trip, then the domain.
     const int64_t t = *a.ctr;
+    const PartStatic st = a.st[p];
+    const PartState q0 = a.state[p], q1 = a.state[(int64_t)a.np + p];
     const bool advance = modes & PL_ADVANCE;
     // The near-item list of step t+2 is touched by nobody during this step.
     if (blockIdx.x == 0 && threadIdx.x == 0 && advance) a.near_cnt[(t + 2) % 3] = 0;
-    if (role_b ? !(modes & (PL_RASTER | PL_MARK)) : !(modes & (PL_FORCES | PL_SWAP | PL_ADVANCE))) return;
-    const PartStatic st = a.st[p];
+    if (role == 0 ? !(modes & (PL_FORCES | PL_SWAP | PL_ADVANCE)) : !(modes & (role == 1 ? PL_RASTER : PL_MARK))) return;
     if (st.dom < 0) return;
-    const DomDev D = a.doms[st.dom];
+    const DomDev D = a.doms[a.one_domain ? 0 : st.dom];  // one domain: loaded without waiting for st
     if (p - D.p0 >= D.np) return;
     const int par = (int)(t & 1);
     const PartState* S0 = a.state + (int64_t)par * a.np;
-    const PartState q = S0[p];
+    const PartState q = par ? q1 : q0;
     const double R = st.R;
     const bool px = D.flags & FLAG_PX, py = D.flags & FLAG_PY;
     typename S::T* base = static_cast<typename S::T*>(a.arena) + D.off;
-    double nxp = q.x, nyp = q.y;
-    if (advance) next_position(D, q, st.fixed, nxp, nyp);
 
     __shared__ __align__(16) unsigned char smem_raw[sizeof(SmemU)];
     SmemU& sm = *reinterpret_cast<SmemU*>(smem_raw);
@@ -285,81 +410,199 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
     __shared__ int sh_warp[PBLOCK / 32];
     __shared__ int near[MAXNEAR];
     __shared__ DiskF near_d[MAXNEAR];
+    // Per-particle quantities the whole CTA uses, computed once: FP64 issue
+    // is scarce on this part, so no warp repeats another's FP64 work.
+    struct Uni {
+        double nxp, nyp;
+        Box bo, bn;  // boxes of the disk at t and at t+1
+        DiskF ko, kn;
+    };
+    __shared__ Uni uni;
+    if (threadIdx.x == 0) {  // the disk at t
+        uni.bo = disk_box(q.x, q.y, R);
+        uni.ko = make_diskf(q.x, q.y, R);
+    } else if (threadIdx.x == 32) {  // the disk at t+1, in another warp so the two FP64 chains overlap
+        double x1 = q.x, y1 = q.y;
+        if (advance) next_position(D, q, st.fixed, x1, y1);
+        uni.nxp = x1;
+        uni.nyp = y1;
+        uni.bn = disk_box(x1, y1, R);
+        uni.kn = make_diskf(x1, y1, R);
+    }
+    __syncthreads();
+    const double nxp = uni.nxp, nyp = uni.nyp;
 
-    if (!role_b) {
+    if (role == 0) {
         // ------------------------------------------------------------------ role A
+        // Warps 0-1: the links, each with the force of Eq. MP1 and then the
+        // exchange of Eqs. MP7-MP8 on the same two slots (they belong to this
+        // link alone); warp 2: covered / uncovered nodes; warps 3-7: the
+        // LJ-type repulsion.  Each warp sums its own terms by shuffles in a
+        // fixed order and thread 0 adds the warps up, so the totals are
+        // deterministic and only the LJ group ever waits on a barrier of its
+        // own before the final one.
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const int32_t* links = a.links + (int64_t)par * a.links_total;
         const int32_t* flips = a.flips + (int64_t)par * a.flips_total;
         const int nl = a.nlinks[(int64_t)par * a.np + p];
         const int nf = a.nflips[(int64_t)par * a.np + p];
+        const bool forces = modes & PL_FORCES, swap = modes & PL_SWAP;
         double acc[DIAG_N];
 #pragma unroll
         for (int c = 0; c < DIAG_N; ++c) acc[c] = 0.0;
-        bool lj_on = false;
-        if (modes & PL_FORCES) {
+        if (warp < 2) {
             // Eq. MP1: F = -2 [f'_k(r_v + e_k, t*) + rho0 omega_k (u_b . e_k) / c_s^2] e_k
-            for (int l = threadIdx.x; l < nl; l += PBLOCK) {
-                const int32_t e = links[st.link_off + l];
-                const int node = e >> 3, k = (e & 7) + 1;
-                const int vy = node / D.pitch, vx = node - vy * D.pitch;
-                int fx = vx + cx(k), fy = vy + cy(k);
-                wrap_node(D, fx, fy);
-                const double fo = full_pop<S>(base, D, opp(k), (int64_t)fy * D.pitch + fx);
-                const double bx = min_image((vx + 0.5 * cx(k)) - q.x, D.nx, px);
-                const double by = min_image((vy + 0.5 * cy(k)) - q.y, D.ny, py);
-                const double ubx = q.U - q.Om * by, uby = q.V + q.Om * bx;
-                const double ube = ubx * cx(k) + uby * cy(k);
-                const double s = -2.0 * (fo + D.rho0 * wgt(k) * ube * 3.0);
-                const double Fx = s * cx(k), Fy = s * cy(k);
-                acc[0] += Fx;
-                acc[1] += Fy;
-                acc[2] += bx * Fy - by * Fx;
+            const A scl = (A)D.scale, inv = (A)D.inv_scale;
+            if (forces || swap) {
+                // four links per thread at a time: all eight slot loads are in
+                // flight before any is used
+#pragma unroll 1
+                for (int l0 = threadIdx.x; l0 < nl; l0 += 4 * 64) {
+                    typename S::T* sa[4];
+                    typename S::T* sb[4];
+                    A va[4], vb[4];
+                    int kk[4], vxs[4], vys[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int l = l0 + 64 * u;
+                        const int32_t e = l < nl ? links[st.link_off + l] : 0;
+                        const int node = e >> 3, k = (e & 7) + 1;
+                        const int vy = node / D.pitch, vx = node - vy * D.pitch;
+                        int fx = vx + cx(k), fy = vy + cy(k);
+                        wrap_node(D, fx, fy);
+                        kk[u] = k;
+                        vxs[u] = vx;
+                        vys[u] = vy;
+                        sa[u] = base + (int64_t)k * D.plane + node;                          // pulled by r_v + e_k
+                        sb[u] = base + (int64_t)opp(k) * D.plane + (int64_t)fy * D.pitch + fx;  // pulled by r_v
+                        if (l < nl) {
+                            va[u] = to_a(*sa[u], inv);
+                            vb[u] = to_a(*sb[u], inv);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (l0 + 64 * u >= nl) break;
+                        const int k = kk[u];
+                        const double bx = min_image((vxs[u] + 0.5 * cx(k)) - q.x, D.nx, px);
+                        const double by = min_image((vys[u] + 0.5 * cy(k)) - q.y, D.ny, py);
+                        const double ubx = q.U - q.Om * by, uby = q.V + q.Om * bx;
+                        const double ube = ubx * cx(k) + uby * cy(k);
+                        if (forces) {
+                            const double fo = S::SHIFT ? (double)vb[u] + wgt(opp(k)) * D.rho0 : (double)vb[u];
+                            const double sF = -2.0 * (fo + D.rho0 * wgt(k) * ube * 3.0);
+                            const double Fx = sF * cx(k), Fy = sF * cy(k);
+                            acc[0] += Fx;
+                            acc[1] += Fy;
+                            acc[2] += bx * Fy - by * Fx;
+                        }
+                        if (swap) {
+                            const A corr = (A)(2.0 * D.rho0 * wgt(k) * ube * 3.0);
+                            from_a(vb[u] + corr, scl, *sa[u]);
+                            from_a(va[u] - corr, scl, *sb[u]);
+                        }
+                    }
+                }
             }
+            if (forces && __any_sync(0xffffffffu, threadIdx.x < nl)) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double x = warp_sum(acc[c]);
+                    if (lane == 0) sm.A.wsum[warp][c] = x;
+                }
+            } else if (lane == 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) sm.A.wsum[warp][c] = 0.0;
+            }
+        } else if (warp == 2) {
             // Covered (+) / uncovered (-) nodes: F = +- rho (u - U_p), with rho and
             // sum f* e of the node at t written by the previous stream-collide pass.
-            for (int l = threadIdx.x; l < nf; l += PBLOCK) {
-                const int32_t e = flips[st.flip_off + l];
-                const int node = e >> 1;
-                const bool cov = e & 1;
-                const int y = node / D.pitch, x = node - y * D.pitch;
-                const double* m = a.flipmom + 3 * ((int64_t)par * a.flips_total + st.flip_off + l);
-                const double r = m[0], jx = m[1], jy = m[2];
-                const double ux = (jx - 0.5 * r * D.gx) / r, uy = (jy - 0.5 * r * D.gy) / r;
-                const double sg = cov ? 1.0 : -1.0;
-                const double Fx = sg * r * (ux - q.U), Fy = sg * r * (uy - q.V);
-                const double rx = min_image(x - q.x, D.nx, px), ry = min_image(y - q.y, D.ny, py);
-                acc[3] += Fx;
-                acc[4] += Fy;
-                acc[5] += rx * Fy - ry * Fx;
-                if (cov) { acc[9] += 1.0; acc[11] += r; }
-                else { acc[10] += 1.0; acc[12] += r; }
+            if (forces) {
+#pragma unroll 1
+                for (int l = lane; l < nf; l += 32) {
+                    const int32_t e = flips[st.flip_off + l];
+                    const int node = e >> 1;
+                    const bool cov = e & 1;
+                    const int y = node / D.pitch, x = node - y * D.pitch;
+                    const double* m = a.flipmom + 3 * ((int64_t)par * a.flips_total + st.flip_off + l);
+                    const double r = m[0], jx = m[1], jy = m[2];
+                    const double ux = (jx - 0.5 * r * D.gx) / r, uy = (jy - 0.5 * r * D.gy) / r;
+                    const double sg = cov ? 1.0 : -1.0;
+                    const double Fx = sg * r * (ux - q.U), Fy = sg * r * (uy - q.V);
+                    const double rx = min_image(x - q.x, D.nx, px), ry = min_image(y - q.y, D.ny, py);
+                    acc[3] += Fx;
+                    acc[4] += Fy;
+                    acc[5] += rx * Fy - ry * Fx;
+                    if (cov) { acc[9] += 1.0; acc[11] += r; }
+                    else { acc[10] += 1.0; acc[12] += r; }
+                }
             }
+            const bool any = forces && nf > 0;
+#pragma unroll
+            for (int c = 3; c < DIAG_N; ++c) {
+                if (c >= 6 && c < 9) continue;
+                const double x = any ? warp_sum(acc[c]) : 0.0;
+                if (lane == 0) sm.A.wsum[2][c] = x;
+            }
+        } else {
             // Eq. MP2 between surface nodes of p and surface nodes of the other
             // particles, and between surface nodes of p and stationary solid /
             // wall nodes, within the threshold r_it.
-            if (D.lj_psi != 0.0) {
-                near_list(a, D, p, S0, q.x, q.y, R, D.lj_rit + 4.0, near, near_d, &nnear, sh_warp);
+            const int gt = (int)threadIdx.x - LJ_W0 * 32;
+            bool on = false;
+            if (forces && D.lj_psi != 0.0) {
+                // other particles within reach, in index order
+                if (gt == 0) nnear = 0;
+                lj_sync();
+                for (int b0 = 0; b0 < D.np; b0 += LJ_NT) {
+                    const int j = b0 + gt, p2 = D.p0 + j;
+                    int hit = 0;
+                    if (j < D.np && p2 != p) {
+                        const PartState o = S0[p2];
+                        float dx = (float)o.x - (float)q.x, dy = (float)o.y - (float)q.y;
+                        if (px) { const float L = (float)D.nx; dx -= L * rintf(dx / L); }
+                        if (py) { const float L = (float)D.ny; dy -= L * rintf(dy / L); }
+                        const float reach = (float)(R + a.st[p2].R + D.lj_rit + 4.0) + 1.0f;
+                        hit = dx * dx + dy * dy <= reach * reach;
+                    }
+                    int excl;
+                    const int tot_hit = lj_scan(hit, gt, sh_warp, excl);
+                    if (hit && nnear + excl < MAXNEAR) {
+                        near[nnear + excl] = p2;
+                        near_d[nnear + excl] = make_diskf(S0[p2].x, S0[p2].y, a.st[p2].R);
+                    }
+                    lj_sync();
+                    if (gt == 0) nnear += tot_hit;
+                    lj_sync();
+                }
                 const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
-                const Box b = disk_box(q.x, q.y, R);
+                const Box b = uni.bo;
                 const Box e = {b.x0 - 1, b.y0 - 1, b.w + 2, b.h + 2};
                 const int reach = (int)floor(D.lj_rit);
                 const bool use_bm = e.n() <= PB_CAP;
                 // 1 = wall or solid node within reach of the box, 0 = fluid or beyond an open end
                 const Box W = {b.x0 - reach, b.y0 - reach, b.w + 2 * reach, b.h + 2 * reach};
                 const bool use_win = W.n() <= PB_CAP;
+                if (gt == 0) sm.A.lj_any = 0;
+                if (use_win) box_status(D, a.solid, W, sm.A.wall_win, gt, LJ_NT);
+                lj_sync();
                 int any_wall = 0;
-                for (int i = threadIdx.x; i < W.n(); i += PBLOCK) {
-                    int wx = W.x0 + i % W.w, wy = W.y0 + i / W.w;
-                    uint8_t v = 0;
-                    if ((D.flags & FLAG_WY) && (wy < 0 || wy >= D.ny)) v = 1;
-                    else if (wrap_node(D, wx, wy)) v = a.solid[D.node_off + (int64_t)wy * D.pitch + wx] != 0;
-                    if (use_win) sm.A.wall_win[i] = v;
-                    any_wall |= v;
+                if (use_win) {
+#pragma unroll 1
+                    for (int i = gt; i < W.n(); i += LJ_NT) {
+                        const uint8_t st4 = sm.A.wall_win[i];
+                        const uint8_t v = (st4 == 1 || st4 == 3) ? 1 : 0;  // solid, or beyond a y wall
+                        sm.A.wall_win[i] = v;
+                        any_wall |= v;
+                    }
                 }
-                lj_on = __syncthreads_or(any_wall) || nn > 0 || !use_win;
-                if (lj_on) {
-                    if (threadIdx.x == 0) lj_n = a.lj_cnt[st.dom];
-                    for (int i = threadIdx.x; i < LJ_TAB; i += PBLOCK) {
+                if (any_wall) sm.A.lj_any = 1;
+                lj_sync();
+                on = sm.A.lj_any != 0 || nn > 0 || !use_win;
+                if (on) {
+                    if (gt == 0) lj_n = a.lj_cnt[st.dom];
+#pragma unroll 1
+                    for (int i = gt; i < LJ_TAB; i += LJ_NT) {
                         const LjEntry en = a.lj_tab[(int64_t)st.dom * LJ_TAB + i];
                         sm.A.lj_ox[i] = en.ox;
                         sm.A.lj_oy[i] = en.oy;
@@ -367,105 +610,145 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
                         sm.A.lj_fy[i] = en.fy;
                     }
                     if (use_bm) {
-                        const DiskF kf = make_diskf(q.x, q.y, R);
-                        for (int i = threadIdx.x; i < e.n(); i += PBLOCK)
+                        const DiskF kf = uni.ko;
+#pragma unroll 1
+                        for (int i = gt; i < e.n(); i += LJ_NT)
                             sm.A.bm[i] = inside_f(D, kf, e.x0 + i % e.w, e.y0 + i / e.w, false) ? 1 : 0;
                     }
-                    __syncthreads();
-                    for (int i = threadIdx.x; i < b.n(); i += PBLOCK) {
-                        const int ay = b.y0 + i / b.w, ax = b.x0 + i % b.w;
-                        bool surf;
-                        if (use_bm) {
-                            const int c = (ay - e.y0) * e.w + (ax - e.x0);
-                            surf = sm.A.bm[c] != 0;
-                            if (surf) {
-                                bool all_in = true;
-#pragma unroll
-                                for (int k = 1; k < 9; ++k) all_in &= sm.A.bm[c + cy(k) * e.w + cx(k)] != 0;
-                                surf = !all_in;
-                            }
-                        } else {
-                            surf = is_surface(D, q.x, q.y, R, ax, ay);
-                        }
-                        if (!surf) continue;
-                        double rax = 0.0, ray = 0.0;
-                        bool arm = false;  // torque arm of this surface node, computed on first use
-                        for (int j = 0; j < nn; ++j) {
-                            const DiskF& ko = near_d[j];
-                            const float ddx = (float)wrap_off(ax - ko.cx, D.nx, px) - ko.fx;
-                            const float ddy = (float)wrap_off(ay - ko.cy, D.ny, py) - ko.fy;
-                            const float lim = (float)(ko.R + D.lj_rit) + 2.0f;
-                            if (ddx * ddx + ddy * ddy > lim * lim) continue;
-                            for (int w = 0; w < lj_n; ++w) {
-                                // node b = a + o expressed in the other particle's own frame
-                                const int bx = ko.cx + wrap_off(ax + sm.A.lj_ox[w] - ko.cx, D.nx, px);
-                                const int by = ko.cy + wrap_off(ay + sm.A.lj_oy[w] - ko.cy, D.ny, py);
-                                if (!is_surface_f(D, ko, bx, by)) continue;
-                                if (!arm) { rax = min_image(ax - q.x, D.nx, px); ray = min_image(ay - q.y, D.ny, py); arm = true; }
-                                acc[6] += sm.A.lj_fx[w];
-                                acc[7] += sm.A.lj_fy[w];
-                                acc[8] += rax * sm.A.lj_fy[w] - ray * sm.A.lj_fx[w];
-                            }
-                        }
+                    // Inside bitmaps of the nearby disks (node offsets -h..h from
+                    // the centre node, h = ceil(R) + 2, which holds every inside
+                    // node and its neighbours): a surface test of theirs becomes
+                    // shared-memory reads of the same FP32 / exact decisions.
+                    if (gt < nn) sm.A.nb_lim[gt] = (float)(near_d[gt].R + D.lj_rit) + 2.0f;
 #pragma unroll 1
-                        for (int j = 0; j < lj_n; ++j) {
-                            int wx = ax + sm.A.lj_ox[j], wy = ay + sm.A.lj_oy[j];
+                    for (int j = 0; j < NB_MAX; ++j) {
+                        int h = 0;
+                        if (j < nn) {
+                            h = (int)ceilf((float)near_d[j].R) + 2;
+                            if (2 * h + 1 > NB_W) h = 0;
+                        }
+                        if (gt == 0) sm.A.nb_h[j] = h;
+                        const int side = 2 * h + 1;
+#pragma unroll 1
+                        for (int c = gt; h > 0 && c < side * side; c += LJ_NT) {
+                            const int ly = c / side, lx = c - ly * side;
+                            sm.A.nbm[j][ly * NB_W + lx] =
+                                inside_f(D, near_d[j], near_d[j].cx + lx - h, near_d[j].cy + ly - h, false) ? 1 : 0;
+                        }
+                    }
+                    lj_sync();
+                    const int ln = lj_n;
+                    // The box in chunks of LJ_NT nodes: compact the chunk's
+                    // surface nodes, then spread (surface node, offset) pairs
+                    // over the group.
+#pragma unroll 1
+                    for (int c0 = 0; c0 < b.n(); c0 += LJ_NT) {
+                        const int i = c0 + gt;
+                        bool surf = false;
+                        if (i < b.n()) {
+                            const int ay = b.y0 + i / b.w, ax = b.x0 + i % b.w;
+                            if (use_bm) {
+                                const int c = (ay - e.y0) * e.w + (ax - e.x0);
+                                surf = sm.A.bm[c] != 0;
+                                if (surf) {
+                                    bool all_in = true;
+#pragma unroll 1
+                                    for (int k = 1; k < 9; ++k) all_in &= sm.A.bm[c + cy(k) * e.w + cx(k)] != 0;
+                                    surf = !all_in;
+                                }
+                            } else {
+                                surf = is_surface(D, q.x, q.y, R, ax, ay);
+                            }
+                        }
+                        int excl;
+                        const int ns = lj_scan(surf ? 1 : 0, gt, sh_warp, excl);
+                        if (surf) {
+                            const int ay = b.y0 + i / b.w, ax = b.x0 + i % b.w;
+                            sm.A.surf[excl] = (int16_t)i;
+                            sm.A.arm[excl] = make_double2(min_image(ax - q.x, D.nx, px), min_image(ay - q.y, D.ny, py));
+                        }
+                        lj_sync();
+#pragma unroll 1
+                        for (int pi = gt; pi < ns * ln; pi += LJ_NT) {
+                            const int si = pi / ln, w = pi - si * ln;
+                            const int i2 = sm.A.surf[si];
+                            const int ay = b.y0 + i2 / b.w, ax = b.x0 + i2 % b.w;
+                            // wall / solid node at a + o_w
+                            int wx = ax + sm.A.lj_ox[w], wy = ay + sm.A.lj_oy[w];
                             bool wall;
                             if (use_win) {
                                 wall = sm.A.wall_win[(wy - W.y0) * W.w + (wx - W.x0)] != 0;
                             } else if ((D.flags & FLAG_WY) && (wy < 0 || wy >= D.ny)) {
                                 wall = true;
                             } else {
-                                if (!wrap_node(D, wx, wy)) continue;
-                                wall = a.solid[D.node_off + (int64_t)wy * D.pitch + wx] != 0;
+                                wall = wrap_node(D, wx, wy) && a.solid[D.node_off + (int64_t)wy * D.pitch + wx] != 0;
                             }
-                            if (!wall) continue;
-                            if (!arm) { rax = min_image(ax - q.x, D.nx, px); ray = min_image(ay - q.y, D.ny, py); arm = true; }
-                            acc[6] += sm.A.lj_fx[j];
-                            acc[7] += sm.A.lj_fy[j];
-                            acc[8] += rax * sm.A.lj_fy[j] - ray * sm.A.lj_fx[j];
+                            int hits = wall ? 1 : 0;
+                            // surface nodes of the other particles at a + o_w
+#pragma unroll 1
+                            for (int j = 0; j < nn; ++j) {
+                                const DiskF& ko = near_d[j];
+                                const float ddx = (float)wrap_off(ax - ko.cx, D.nx, px) - ko.fx;
+                                const float ddy = (float)wrap_off(ay - ko.cy, D.ny, py) - ko.fy;
+                                const float lim = sm.A.nb_lim[j];
+                                if (ddx * ddx + ddy * ddy > lim * lim) continue;
+                                // node b = a + o expressed in the other particle's own frame
+                                const int ox = wrap_off(ax + sm.A.lj_ox[w] - ko.cx, D.nx, px);
+                                const int oy = wrap_off(ay + sm.A.lj_oy[w] - ko.cy, D.ny, py);
+                                const int h = j < NB_MAX ? sm.A.nb_h[j] : 0;
+                                bool surf_b;
+                                if (h > 0) {
+                                    surf_b = false;
+                                    if (ox > -h && ox < h && oy > -h && oy < h) {
+                                        const uint8_t* m = sm.A.nbm[j] + (oy + h) * NB_W + (ox + h);
+                                        if (*m) {
+                                            bool all_in = true;
+#pragma unroll 1
+                                            for (int k = 1; k < 9; ++k) all_in &= m[cy(k) * NB_W + cx(k)] != 0;
+                                            surf_b = !all_in;
+                                        }
+                                    }
+                                } else {
+                                    surf_b = is_surface_f(D, ko, ko.cx + ox, ko.cy + oy);
+                                }
+                                if (surf_b) ++hits;
+                            }
+                            if (hits) {
+                                const double rax = sm.A.arm[si].x, ray = sm.A.arm[si].y;
+                                const double fxw = sm.A.lj_fx[w] * hits, fyw = sm.A.lj_fy[w] * hits;
+                                acc[6] += fxw;
+                                acc[7] += fyw;
+                                acc[8] += rax * fyw - ray * fxw;
+                            }
                         }
+                        lj_sync();
                     }
                 }
             }
-            // component groups: links 0-2, covered/uncovered 3-5 and 9-12, LJ 6-8
-            if (threadIdx.x < DIAG_N) tot[threadIdx.x] = 0.0;
-            __syncthreads();
-            if (nl > 0) block_sum_range<DIAG_N>(acc, 0, 3, sm.A.red, tot);
-            if (nf > 0) {
-                block_sum_range<DIAG_N>(acc, 3, 6, sm.A.red, tot);
-                block_sum_range<DIAG_N>(acc, 9, 13, sm.A.red, tot);
+#pragma unroll
+            for (int c = 6; c < 9; ++c) {
+                const double x = on ? warp_sum(acc[c]) : 0.0;
+                if (lane == 0) sm.A.wsum[warp][c] = x;
             }
-            if (lj_on) block_sum_range<DIAG_N>(acc, 6, 9, sm.A.red, tot);
-            if (threadIdx.x < DIAG_N) a.diag[(int64_t)p * DIAG_N + threadIdx.x] = tot[threadIdx.x];
         }
-        // Eqs. MP7-MP8 on the links of the rasterisation at t with u_b(t); every
-        // read of these slots above happened before this barrier.
         __syncthreads();
-        if (modes & PL_SWAP) {
-            const A scl = (A)D.scale, inv = (A)D.inv_scale;
-            for (int l = threadIdx.x; l < nl; l += PBLOCK) {
-                const int32_t e = links[st.link_off + l];
-                const int node = e >> 3, k = (e & 7) + 1;
-                const int vy = node / D.pitch, vx = node - vy * D.pitch;
-                int fx = vx + cx(k), fy = vy + cy(k);
-                wrap_node(D, fx, fy);
-                const double bx = min_image((vx + 0.5 * cx(k)) - q.x, D.nx, px);
-                const double by = min_image((vy + 0.5 * cy(k)) - q.y, D.ny, py);
-                const double ubx = q.U - q.Om * by, uby = q.V + q.Om * bx;
-                const A corr = (A)(2.0 * D.rho0 * wgt(k) * (ubx * cx(k) + uby * cy(k)) * 3.0);
-                typename S::T* sa = base + (int64_t)k * D.plane + node;                          // pulled by r_v + e_k
-                typename S::T* sb = base + (int64_t)opp(k) * D.plane + (int64_t)fy * D.pitch + fx;  // pulled by r_v
-                const A va = to_a(*sa, inv), vb = to_a(*sb, inv);
-                from_a(vb + corr, scl, *sa);
-                from_a(va - corr, scl, *sb);
-            }
+        if (forces && threadIdx.x < DIAG_N) {
+            // component groups: links 0-2 (warps 0-1), covered/uncovered 3-5 and
+            // 9-12 (warp 2), LJ 6-8 (warps 3-7); fixed order
+            const int c = threadIdx.x;
+            double x = 0.0;
+            if (c < 3) x = sm.A.wsum[0][c] + sm.A.wsum[1][c];
+            else if (c < 6 || c >= 9) x = sm.A.wsum[2][c];
+            else x = (((sm.A.wsum[3][c] + sm.A.wsum[4][c]) + sm.A.wsum[5][c]) + sm.A.wsum[6][c]) + sm.A.wsum[7][c];
+            tot[c] = x;
+            a.diag[(int64_t)p * DIAG_N + c] = x;
         }
+        __syncthreads();
         if (advance && threadIdx.x == 0) {
             // Eqs. MP5, MP6 (velocities) with r_c(t+1) = r_c(t) + U_p(t).
             PartState n = q;
             if (!st.fixed) {
-                if (modes & PL_FORCES) {
+                if (forces) {
                     const double Fx = (tot[0] + tot[3]) + tot[6], Fy = (tot[1] + tot[4]) + tot[7];
                     const double T = (tot[2] + tot[5]) + tot[8];
                     n.U = q.U + Fx * st.inv_m + st.buoy * D.gx;
@@ -482,16 +765,16 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
         return;
     }
 
-    // ---------------------------------------------------------------------- role B
     const int64_t t_next = advance ? t + 1 : t;
     const int wpar = (int)(t_next & 1);
-    if (modes & PL_MARK) {
+    if (role == 2) {
+        // ------------------------------------------------------------------ role C
         // Work items (row segments) within two nodes of the disk's boxes at t
         // and t+1 are "near": the stream-collide pass of that step runs them
         // after this kernel, and they hold every node that changes side.
         const int mpar = (int)(t_next & 1);
         const int lpar = (int)(t_next % 3);
-        const Box bo = disk_box(q.x, q.y, R), bn = disk_box(nxp, nyp, R);
+        const Box bo = uni.bo, bn = uni.bn;
         const int x0 = min(bo.x0, bn.x0) - 2, x1 = max(bo.x0 + bo.w, bn.x0 + bn.w) + 1;
         const int y0 = min(bo.y0, bn.y0) - 2, y1 = max(bo.y0 + bo.h, bn.y0 + bn.h) + 1;
         const int seg_w = 32 * D.V;
@@ -512,8 +795,10 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
                 if (xc == x1) break;
             }
         }
+        return;
     }
-    if (!(modes & PL_RASTER)) return;
+
+    // ---------------------------------------------------------------------- role B
 
     // Particles whose disks at t+1 may touch this one's: they bound the exterior
     // nodes of the new links and reveal overlaps.
@@ -529,7 +814,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
     }
     // Union of the old and new boxes; every neighbour of a node inside either
     // disk lies in it.
-    const Box bo = disk_box(q.x, q.y, R), bn = disk_box(nxp, nyp, R);
+    const Box bo = uni.bo, bn = uni.bn;
     Box U;
     U.x0 = min(bo.x0, bn.x0);
     U.y0 = min(bo.y0, bn.y0);
@@ -537,90 +822,123 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
     U.h = max(bo.y0 + bo.h, bn.y0 + bn.h) - U.y0;
     const bool use_bm = U.n() <= PB_CAP;
     if (use_bm) {
-        const DiskF kn = make_diskf(nxp, nyp, R), ko = make_diskf(q.x, q.y, R);
+        // 0 = fluid node in the domain, 1 = solid, 2 = outside the domain
+        box_status(D, a.solid, U, sm.B.node_st, threadIdx.x, PBLOCK);
+        const DiskF kn = uni.kn, ko = uni.ko;
+#pragma unroll 1
         for (int i = threadIdx.x; i < U.n(); i += PBLOCK) {
             const int xu = U.x0 + i % U.w, yu = U.y0 + i / U.w;
             sm.B.bnew[i] = inside_f(D, kn, xu, yu, true) ? 1 : 0;
             sm.B.bold[i] = advance ? (inside_f(D, ko, xu, yu, true) ? 1 : 0) : sm.B.bnew[i];
-            // 0 = fluid node in the domain, 1 = solid, 2 = outside an open end
-            int x = xu, y = yu;
-            sm.B.node_st[i] = wrap_node(D, x, y) ? (a.solid[D.node_off + (int64_t)y * D.pitch + x] ? 1 : 0) : 2;
+            if (sm.B.node_st[i] == 3) sm.B.node_st[i] = 2;
         }
     }
     __syncthreads();
-    auto in_new = [&](int xu, int yu) -> bool {
-        if (use_bm) return sm.B.bnew[(yu - U.y0) * U.w + (xu - U.x0)] != 0;
-        int x = xu, y = yu;
-        if (!wrap_node(D, x, y)) { x = xu; y = yu; }
-        return inside_disk(D, nxp, nyp, R, x, y);
-    };
-    auto in_old = [&](int xu, int yu) -> bool {
-        if (use_bm) return sm.B.bold[(yu - U.y0) * U.w + (xu - U.x0)] != 0;
-        int x = xu, y = yu;
-        if (!wrap_node(D, x, y)) { x = xu; y = yu; }
-        return inside_disk(D, q.x, q.y, R, x, y);
-    };
+    RastCtx rc;
+    rc.D = a.doms + st.dom;
+    rc.solid = a.solid;
+    rc.sm = &sm.B;
+    rc.near_d = near_d;
+    rc.nn = nn;
+    rc.U = U;
+    rc.use_bm = use_bm;
+    rc.advance = advance;
+    rc.nxp = nxp;
+    rc.nyp = nyp;
+    rc.qx = q.x;
+    rc.qy = q.y;
+    rc.R = R;
     int32_t* links = a.links + (int64_t)wpar * a.links_total;
     int32_t* flips = a.flips + (int64_t)wpar * a.flips_total;
     const int64_t stamp = (int64_t)(int32_t)(t + 1) << 32;
-    int ltotal = 0, ftotal = 0;
+    // Each thread takes a contiguous run of the box, so one block scan per
+    // list places every entry, in lattice order: classify and count, scan,
+    // then write (from the stored classification when the box has a bitmap).
+    const int nU = U.n();
+    const int per = (nU + PBLOCK - 1) / PBLOCK;
+    const int i0 = (int)threadIdx.x * per, i1 = min(nU, i0 + per);
     bool overlap = false;
-    for (int t0 = 0; t0 < U.n(); t0 += PBLOCK) {
-        const int i = t0 + threadIdx.x;
-        uint32_t mask = 0;
-        int node = 0, fcode = 0, fc = 0;
-        if (i < U.n()) {
-            const int xu = U.x0 + i % U.w, yu = U.y0 + i / U.w;
-            int x = xu, y = yu;
-            if (wrap_node(D, x, y)) {
-                node = y * D.pitch + x;
-                const bool solid_here = use_bm ? sm.B.node_st[i] == 1 : a.solid[D.node_off + node] != 0;
-                const bool now = in_new(xu, yu);
-                if (now) {
-                    for (int j = 0; j < nn; ++j)
-                        if (inside_f(D, near_d[j], xu, yu, true)) overlap = true;
-                    if (!solid_here) {
+    int lcount = 0, fcount = 0;
+    if (use_bm) {
+        // Bitmap path, inline: every test is a shared-memory read.
 #pragma unroll 1
+        for (int i = i0; i < i1; ++i) {
+            const uint8_t st0 = sm.B.node_st[i];
+            uint32_t r = 0;
+            if (st0 != 2) {
+                const bool now = sm.B.bnew[i] != 0;
+                if (now) {
+                    r = 1u << 10;
+                    if (nn > 0) {
+                        const int xu = U.x0 + i % U.w, yu = U.y0 + i / U.w;
+#pragma unroll 1
+                        for (int j = 0; j < nn; ++j)
+                            if (inside_f(D, near_d[j], xu, yu, true)) overlap = true;
+                    }
+                    if (st0 == 0) {
+#pragma unroll
                         for (int k = 1; k < 9; ++k) {
-                            const int fxu = xu + cx(k), fyu = yu + cy(k);
-                            if (use_bm) {
-                                if (sm.B.node_st[(fyu - U.y0) * U.w + (fxu - U.x0)] != 0) continue;
-                            } else {
-                                int fx = fxu, fy = fyu;
-                                if (!wrap_node(D, fx, fy)) continue;
-                                if (a.solid[D.node_off + (int64_t)fy * D.pitch + fx]) continue;
+                            const int jn = i + cy(k) * U.w + cx(k);
+                            if (sm.B.node_st[jn] != 0 || sm.B.bnew[jn] != 0) continue;
+                            bool in_any = false;
+                            if (nn > 0) {
+                                const int fxu = U.x0 + jn % U.w, fyu = U.y0 + jn / U.w;
+#pragma unroll 1
+                                for (int j = 0; j < nn && !in_any; ++j) in_any = inside_f(D, near_d[j], fxu, fyu, true);
                             }
-                            bool in_any = in_new(fxu, fyu);
-                            for (int j = 0; j < nn && !in_any; ++j) in_any = inside_f(D, near_d[j], fxu, fyu, true);
-                            if (!in_any) mask |= 1u << k;
+                            if (!in_any) r |= 1u << k;
                         }
                     }
                 }
-                if (advance && !solid_here && now != in_old(xu, yu)) {
-                    fc = 1;
-                    fcode = (node << 1) | (now ? 1 : 0);
-                }
+                if (advance && st0 == 0 && now != (sm.B.bold[i] != 0)) r |= 1u << 9;
             }
+            sm.B.res[i] = (uint16_t)r;
+            lcount += __popc(r & 0x1FEu);
+            fcount += (r >> 9) & 1u;
         }
-        int excl;
-        const int tot_l = block_scan(__popc(mask), sh_warp, excl);
-        int w = ltotal + excl;
+    } else {
+#pragma unroll 1
+        for (int i = i0; i < i1; ++i) {
+            int node;
+            const uint32_t r = node_info(rc, i, node, overlap);
+            lcount += __popc(r & 0x1FEu);
+            fcount += (r >> 9) & 1u;
+        }
+    }
+    int lex, fex;
+    const int ltotal = block_scan(lcount, sh_warp, lex);
+    const int ftotal = block_scan(fcount, sh_warp, fex);
+#pragma unroll 1
+    for (int i = i0; i < i1 && (lcount | fcount); ++i) {
+        int node = 0;
+        uint32_t r;
+        if (use_bm) {
+            r = sm.B.res[i];
+            if (r) {
+                int x = U.x0 + i % U.w, y = U.y0 + i / U.w;
+                wrap_node(D, x, y);
+                node = y * D.pitch + x;
+            }
+        } else {
+            bool dummy = false;
+            r = node_info(rc, i, node, dummy);
+        }
+#pragma unroll 1
         for (int k = 1; k < 9; ++k)
-            if (mask & (1u << k)) {
-                if (w < st.link_cap) links[st.link_off + w] = (node << 3) | (k - 1);
-                ++w;
+            if (r & (1u << k)) {
+                if (lex < st.link_cap) links[st.link_off + lex] = (node << 3) | (k - 1);
+                ++lex;
             }
-        ltotal += tot_l;
-        int fex;
-        const int tot_f = block_scan(fc, sh_warp, fex);
-        if (fc && ftotal + fex < st.flip_cap) {
-            const int64_t idx = st.flip_off + ftotal + fex;
-            flips[idx] = fcode;
-            // the stream-collide pass of this step leaves this node's moments in flipmom[slot]
-            const int64_t slot = (int64_t)wpar * a.flips_total + idx;
-            a.fliptag[D.node_off + node] = stamp | (uint32_t)slot;
+        if ((r >> 9) & 1u) {
+            if (fex < st.flip_cap) {
+                const int64_t idx = st.flip_off + fex;
+                flips[idx] = (node << 1) | (int)((r >> 10) & 1u);
+                // the stream-collide pass of this step leaves this node's moments in flipmom[slot]
+                const int64_t slot = (int64_t)wpar * a.flips_total + idx;
+                a.fliptag[D.node_off + node] = stamp | (uint32_t)slot;
+            }
+            ++fex;
         }
-        ftotal += tot_f;
     }
     if (overlap || ltotal > st.link_cap || ftotal > st.flip_cap) atomicOr(a.err, ERR_STATE);
     if (threadIdx.x == 0) {
@@ -641,7 +959,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
 
 cudaError_t launch_particle_step(int kind, const PartArgs& a, int modes, cudaStream_t s) {
     if (a.np <= 0) return cudaSuccess;
-    LBM_PDISPATCH(kind, (k_particle_step<S><<<2 * a.np, PBLOCK, 0, s>>>(a, modes)));
+    LBM_PDISPATCH(kind, (k_particle_step<S><<<3 * a.np, PBLOCK, 0, s>>>(a, modes)));
     return cudaGetLastError();
 }
 

@@ -75,6 +75,7 @@ constexpr int CHECK_BLOCKS = 304;
 // ---- particle kernel (k_part.cu) ----
 struct PartArgs {
     const DomDev* doms;
+    int one_domain;            // 1 when the context has a single domain (its descriptor needs no lookup)
     void* arena;               // populations holding f*(t) (read for forces, link slots exchanged)
     const uint8_t* solid;
     PartState* state;          // [2][np]: state at step t in slot (t & 1)
