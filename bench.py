@@ -27,6 +27,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) per full stream-collide launch, from one ncu capture of the
+# current kernel version on this workload (a FAR launch, scaled by the share of work
+# items it processed).  Any change to the kernel voids it.
+NCU_TRAFFIC = {("k_stream_collide", "f32s", 2048, 1024): 106.2e6}
+
 METRIC = "D2Q9 MLUPS and % HBM roofline, FP32/FP16-store vs FP64 path at stated error"
 UNIT = "MLUPS"
 STORE_BYTES = {"f64": 8, "f32": 4, "f32s": 4, "f16s": 2, "bf16s": 2}
@@ -188,6 +193,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--profile-steps", type=int, default=500)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch", default=None,
+                    help="stream-collide kernel,block,stages (e.g. 1,128,0); skips the autotuner")
     ap.add_argument("--nx", type=int, default=2048)
     ap.add_argument("--ny", type=int, default=1024)
     args = ap.parse_args()
@@ -220,7 +227,9 @@ def main():
         return lbm.Context(p, stream=stream.cuda_stream, solids=[w.solid], particles=[w.particles])
 
     ctx = make_ctx(args.store)
-    if not args.no_autotune:
+    if args.launch:
+        ctx.set_launch(*[int(v) for v in args.launch.split(",")])
+    elif not args.no_autotune:
         ctx.autotune(20)
     kernels_per_step = 3 if w.particles else 1  # far stream-collide, particle step, near stream-collide
 
@@ -266,8 +275,9 @@ def main():
     achieved = alg_bytes / (k1_ms * 1e-3) / 1e9
     launch = ctx.launch()
     k1_name = "k_stream_staged" if launch[0] == 2 else "k_stream_collide"
+    traffic = NCU_TRAFFIC.get((k1_name, args.store, w.nx, w.ny))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": k1_name, "peak_source": peak_kind,
+                "traffic": traffic, "kernel": k1_name, "peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "kernel_ms": k1_ms,
                 "kernel_share": kk / max(kf + kl + kk, 1e-9),
                 "particle_kernel_ms": kf / args.profile_steps,
