@@ -181,6 +181,75 @@ def run_reference(args):
     return 0
 
 
+def ensemble_bench(lbm, workloads, stream, steps32: int, steps64: int, samples: int):
+    """The 96-domain fluctuating-LB ensemble (uneven sizes, per-domain Philox seed and kT,
+    one R = 5 Brownian disk each): all domains in one context and one launch per step
+    (shifted FP32 store, autotuned, CUDA graph), against one FP64 context per domain
+    (per-domain launches, each context on its own stream).  Both report aggregate MLUPS;
+    the FP32 run also reports the equilibrium statistics of fluid and particles."""
+    import torch
+    ws = workloads.ensemble()
+    nodes = sum(w.nx * w.ny for w in ws)
+
+    def params(w, store):
+        return lbm.make_params(nx=w.nx, ny=w.ny, store=store, max_particles=len(w.particles), **w.params)
+
+    out = {"domains": len(ws), "nodes": nodes, "sizes": sorted({(w.nx, w.ny) for w in ws})}
+    ctx = lbm.Context([params(w, "f32s") for w in ws], stream=stream.cuda_stream, particles=[w.particles for w in ws])
+    ctx.autotune(10)
+    ctx.step(500)
+    ctx.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(steps32)
+    e1.record(stream)
+    e1.synchronize()
+    ctx.sync()
+    ms = e0.elapsed_time(e1)
+    out["f32s_one_launch"] = {"MLUPS": nodes * steps32 / (ms * 1e-3) / 1e6, "steps": steps32,
+                              "launch": list(ctx.launch())}
+    # equilibrium statistics: <rho u_a^2> = kT per node (fluid), <U_a^2> = kT / M (disks)
+    fl, pu = [], []
+    for _ in range(samples):
+        ctx.step(50)
+        for d, w in enumerate(ws):
+            kT = w.params["kT"]
+            rho, ux, uy = ctx.moments(dom=d)
+            fl.append((float((rho * ux * ux).mean()) / kT, float((rho * uy * uy).mean()) / kT))
+            q = ctx.particles(dom=d)[0]
+            M = q["rho_p"] * np.pi * q["R"] ** 2
+            pu.append((q["U"] ** 2 * M / kT, q["V"] ** 2 * M / kT))
+    fl = np.array(fl)
+    pu = np.array(pu)
+    out["fluid_rho_u2_over_kT"] = {"x": float(fl[:, 0].mean()), "y": float(fl[:, 1].mean()),
+                                   "samples": int(len(fl))}
+    # disk velocity samples 50 steps apart are treated as independent for the interval
+    pm = pu.mean()
+    out["particle_M_U2_over_kT"] = {"mean": float(pm), "ci95": float(1.96 * pu.std() / np.sqrt(pu.size)),
+                                    "samples": int(pu.size)}
+    ctx.close()
+    # per-domain launches of the FP64 path
+    side = [torch.cuda.Stream() for _ in ws]
+    ctxs = [lbm.Context(params(w, "f64"), stream=side[d].cuda_stream, particles=[w.particles])
+            for d, w in enumerate(ws)]
+    for c in ctxs:
+        c.step(20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in ctxs:
+        c.step(steps64)
+    for c in ctxs:
+        c.sync()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    out["f64_per_domain"] = {"MLUPS": nodes * steps64 / t / 1e6, "steps": steps64,
+                             "timing": "wall clock around the enqueue of every context and a sync of all"}
+    for c in ctxs:
+        c.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -193,6 +262,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--profile-steps", type=int, default=500)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-steps", type=int, default=4000)
     ap.add_argument("--launch", default=None,
                     help="stream-collide kernel,block,stages (e.g. 1,128,0); skips the autotuner")
     ap.add_argument("--nx", type=int, default=2048)
@@ -335,6 +406,11 @@ def main():
                                "frac": b3 / (k3 / 100 * 1e-3) / 1e9 / peak}
             c3.close()
 
+    ens = None
+    if rank == 0 and not args.no_ensemble:
+        from paper_2006_12910_gb300 import workloads as _wl
+        ens = ensemble_bench(lbm, _wl, stream, args.ensemble_steps, max(100, args.ensemble_steps // 20), 20)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, t, cores = cpu_oracle_mlups(w, budget_s=15.0)
@@ -352,7 +428,7 @@ def main():
                            "launch": {"kernel": k1_name, "block": launch[1], "stages": launch[2],
                                       "grid": launch[3], "graph_steps": 8}},
                 "clocks": clk, "gpu_launches": args.steps * kernels_per_step,
-                "roofline": roofline, "e2e": e2e, "variants": variants, "cpu_baseline": cpu}
+                "roofline": roofline, "e2e": e2e, "variants": variants, "ensemble": ens, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
