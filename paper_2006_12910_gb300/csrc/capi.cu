@@ -72,14 +72,16 @@ struct lbm_ctx {
     cudaStream_t side = nullptr;
     cudaStream_t far_stream = nullptr;   // branch running the far stream-collide items
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_far[2] = {nullptr, nullptr}, ev_near[2] = {nullptr, nullptr};  // per-step edges inside a graph
     bool overlap = true;                 // far items run concurrently with the particle kernels
-    int32_t* mark = nullptr;             // [2][total_items]
+    int32_t* mark = nullptr;             // [3][total_items]
     int32_t* near_list = nullptr;        // [3][total_items]
     int32_t* near_cnt = nullptr;         // [3]
     int64_t* fliptag = nullptr;          // per node
     double* flipmom = nullptr;           // [2][flips_total][3]
     int64_t near_grid = 1;
     LjEntry* lj_tab = nullptr;           // [ndom][LJ_TAB]
+    double2* ljwall = nullptr;           // per node: Eq. MP2 force from walls / solids (domains with psi > 0)
     int32_t* lj_cnt = nullptr;           // [ndom]
     cudaEvent_t ev_snap = nullptr, ev_copied = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -297,6 +299,7 @@ PartArgs part_args(lbm_ctx* c, int cur) {
     PartArgs a;
     a.doms = c->dd;
     a.one_domain = c->ndom == 1;
+    a.dom0 = c->hd[0];
     a.arena = c->f[cur];
     a.solid = c->solid;
     a.state = c->pstate;
@@ -317,6 +320,7 @@ PartArgs part_args(lbm_ctx* c, int cur) {
     a.near_list = c->near_list;
     a.near_cnt = c->near_cnt;
     a.total_items = c->total_items;
+    a.ljwall = c->ljwall;
     a.lj_tab = c->lj_tab;
     a.lj_cnt = c->lj_cnt;
     return a;
@@ -367,13 +371,42 @@ cudaError_t enqueue_step(lbm_ctx* c, int cur, cudaStream_t s) {
     return cudaStreamWaitEvent(s, c->ev_join, 0);
 }
 
+// GRAPH_STEPS steps with particles, as two chains: on the main stream the
+// particle kernel and NEAR pass of every step, on the far stream the FAR
+// passes; FAR(t) waits only for NEAR(t-1) and NEAR(t) only for FAR(t-1).  So
+// the particle kernel of t+1 can start while FAR(t) is still running (it reads
+// and writes only slots near the particles, which NEAR(t) produced and FAR
+// never touches), and FAR(t+1) can start while the particle kernel of t+1
+// runs.  Marks are three-way and both passes publish the step counter, so no
+// kernel of one chain reads what a concurrent kernel of the other writes.
+cudaError_t enqueue_graph_chains(lbm_ctx* c, int k, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaEventRecord(c->ev_fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c->far_stream, c->ev_fork, 0)) != cudaSuccess) return e;
+    for (int st = 0; st < GRAPH_STEPS; ++st) {
+        const int cur = k ^ (st & 1);
+        const PartArgs a = part_args(c, cur);
+        if (st > 0 && (e = cudaStreamWaitEvent(c->far_stream, c->ev_near[(st - 1) & 1], 0)) != cudaSuccess) return e;
+        if ((e = enqueue_stream_collide(c, cur, c->far_stream, c->block, c->grid, STREAM_FAR)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(c->ev_far[st & 1], c->far_stream)) != cudaSuccess) return e;
+        if ((e = launch_particle_step(c->kind, a, PL_STEP, s)) != cudaSuccess) return e;
+        if (st > 0 && (e = cudaStreamWaitEvent(s, c->ev_far[(st - 1) & 1], 0)) != cudaSuccess) return e;
+        if ((e = enqueue_stream_collide(c, cur, s, c->block, c->near_grid, STREAM_NEAR)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(c->ev_near[st & 1], s)) != cudaSuccess) return e;
+    }
+    if ((e = cudaEventRecord(c->ev_join, c->far_stream)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(s, c->ev_join, 0);
+}
+
 int build_graphs(lbm_ctx* c) {
     for (int k = 0; k < 2; ++k) {
         if (c->gexec[k]) { cudaGraphExecDestroy(c->gexec[k]); c->gexec[k] = nullptr; }
         cudaGraph_t g = nullptr;
         CKC(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
-        for (int s = 0; s < GRAPH_STEPS && e == cudaSuccess; ++s) e = enqueue_step(c, k ^ (s & 1), c->cap_stream);
+        if (c->np_active > 0 && c->overlap) e = enqueue_graph_chains(c, k, c->cap_stream);
+        else
+            for (int s = 0; s < GRAPH_STEPS && e == cudaSuccess; ++s) e = enqueue_step(c, k ^ (s & 1), c->cap_stream);
         cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
         if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); CKC(c, e); }
         CKC(c, e2);
@@ -422,6 +455,10 @@ int upload_geometry(lbm_ctx* c, int dom) {
     CKC(c, cudaMemcpy(c->nflags + D.node_off, fl.data(), fl.size() * 2, cudaMemcpyHostToDevice));
     if (!words.empty())
         CKC(c, cudaMemcpy(c->special + D.mask_off, words.data(), words.size() * 4, cudaMemcpyHostToDevice));
+    if (c->ljwall && c->prm[dom].lj_psi > 0.0) {
+        CKC(c, launch_lj_wall(D, c->solid, c->lj_tab, c->lj_cnt, dom, c->ljwall, c->stream));
+        CKC(c, cudaStreamSynchronize(c->stream));
+    }
     return LBM_OK;
 }
 
@@ -519,10 +556,14 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
     CKCR(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     CKCR(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     CKCR(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
-    CKCR(cudaMalloc(&c->mark, sizeof(int32_t) * 2 * std::max<int64_t>(1, c->total_items)));
+    for (int k = 0; k < 2; ++k) {
+        CKCR(cudaEventCreateWithFlags(&c->ev_far[k], cudaEventDisableTiming));
+        CKCR(cudaEventCreateWithFlags(&c->ev_near[k], cudaEventDisableTiming));
+    }
+    CKCR(cudaMalloc(&c->mark, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items)));
     CKCR(cudaMalloc(&c->near_list, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items)));
     CKCR(cudaMalloc(&c->near_cnt, sizeof(int32_t) * 3));
-    CKCR(cudaMemsetAsync(c->mark, 0xff, sizeof(int32_t) * 2 * std::max<int64_t>(1, c->total_items), c->stream));
+    CKCR(cudaMemsetAsync(c->mark, 0xff, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items), c->stream));
     CKCR(cudaMemsetAsync(c->near_cnt, 0, sizeof(int32_t) * 3, c->stream));
     CKCR(cudaMalloc(&c->fliptag, sizeof(int64_t) * std::max<size_t>(1, c->node_bytes)));
     CKCR(cudaMemsetAsync(c->fliptag, 0xff, sizeof(int64_t) * std::max<size_t>(1, c->node_bytes), c->stream));
@@ -559,6 +600,14 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
     CKCR(cudaMalloc(&c->solid, c->node_bytes));
     CKCR(cudaMalloc(&c->nflags, c->node_bytes * 2));
     CKCR(cudaMalloc(&c->special, std::max<size_t>(1, c->special_words) * 4));
+    {
+        bool any_lj = false;
+        for (int d = 0; d < ndom; ++d) any_lj |= per_domain[d].lj_psi > 0.0 && per_domain[d].lj_rit > 0.0;
+        if (any_lj) {
+            CKCR(cudaMalloc(&c->ljwall, sizeof(double2) * std::max<size_t>(1, c->node_bytes)));
+            CKCR(cudaMemsetAsync(c->ljwall, 0, sizeof(double2) * std::max<size_t>(1, c->node_bytes), c->stream));
+        }
+    }
     CKCR(cudaMalloc(&c->dd, sizeof(DomDev) * ndom));
     CKCR(cudaMalloc(&c->d_item_off, sizeof(int64_t) * ndom));
     CKCR(cudaMalloc(&c->ctr, sizeof(int64_t) * 2));
@@ -602,9 +651,14 @@ void lbm_destroy(lbm_ctx* c) {
     if (c->h_mom) cudaFreeHost(c->h_mom);
     free_particles(c);
     cudaFree(c->mark); cudaFree(c->near_list); cudaFree(c->near_cnt); cudaFree(c->lj_tab); cudaFree(c->lj_cnt);
+    cudaFree(c->ljwall);
     cudaFree(c->fliptag);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    for (int k = 0; k < 2; ++k) {
+        if (c->ev_far[k]) cudaEventDestroy(c->ev_far[k]);
+        if (c->ev_near[k]) cudaEventDestroy(c->ev_near[k]);
+    }
     if (c->far_stream) cudaStreamDestroy(c->far_stream);
     if (c->ev_snap) cudaEventDestroy(c->ev_snap);
     if (c->ev_copied) cudaEventDestroy(c->ev_copied);
@@ -707,7 +761,7 @@ int lbm_add_particles(lbm_ctx* c, int dom, int n, const lbm_particle* p) {
     c->flips_total = fo;
     // rasterise every particle at its current position (no link exchange, no
     // flips) and mark the work items near the particles for the next step
-    CKC(c, cudaMemsetAsync(c->mark, 0xff, sizeof(int32_t) * 2 * std::max<int64_t>(1, c->total_items), c->stream));
+    CKC(c, cudaMemsetAsync(c->mark, 0xff, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items), c->stream));
     CKC(c, cudaMemsetAsync(c->near_cnt, 0, sizeof(int32_t) * 3, c->stream));
     CKC(c, launch_particle_step(c->kind, part_args(c, c->cur), PL_RASTER | PL_MARK, c->stream));
     c->graph_dirty = true;
@@ -1010,7 +1064,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
         for (int d = 0; d < c->ndom; ++d) c->hd[d].np = dnp[d];
         c->np_active = np_total;
         CKC(c, cudaMemcpy(c->dd, c->hd.data(), sizeof(DomDev) * c->ndom, cudaMemcpyHostToDevice));
-        CKC(c, cudaMemset(c->mark, 0xff, sizeof(int32_t) * 2 * std::max<int64_t>(1, c->total_items)));
+        CKC(c, cudaMemset(c->mark, 0xff, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items)));
         CKC(c, cudaMemset(c->near_cnt, 0, sizeof(int32_t) * 3));
         CKC(c, launch_particle_step(c->kind, part_args(c, c->cur), PL_MARK, c->stream));
         CKC(c, cudaStreamSynchronize(c->stream));

@@ -62,6 +62,39 @@ __global__ void k_prime_mail(DomDev D, typename S::T* arena, const uint16_t* nfl
     }
 }
 
+__global__ void k_lj_wall(DomDev D, const uint8_t* solid, const LjEntry* tab, const int32_t* cnt, int dom, double2* out) {
+    const int64_t n = (int64_t)D.nx * D.ny;
+    const int m = cnt[dom];
+    const LjEntry* t = tab + (int64_t)dom * LJ_TAB;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(k / D.nx), x = (int)(k - (int64_t)y * D.nx);
+        const int64_t ni = D.node_off + (int64_t)y * D.pitch + x;
+        double fx = 0.0, fy = 0.0;
+        if (!solid[ni]) {
+            for (int j = 0; j < m; ++j) {
+                int wx = x + t[j].ox, wy = y + t[j].oy;
+                bool wall = false;
+                if (wy < 0 || wy >= D.ny) {
+                    if (D.flags & FLAG_WY) wall = true;
+                    else wy = wy < 0 ? wy + D.ny : wy - D.ny;
+                }
+                if (!wall) {
+                    if (wx < 0 || wx >= D.nx) {
+                        if (!(D.flags & FLAG_PX)) continue;
+                        wx = wx < 0 ? wx + D.nx : wx - D.nx;
+                    }
+                    wall = solid[D.node_off + (int64_t)wy * D.pitch + wx] != 0;
+                }
+                if (wall) {
+                    fx += t[j].fx;
+                    fy += t[j].fy;
+                }
+            }
+        }
+        out[ni] = make_double2(fx, fy);
+    }
+}
+
 template <class S>
 __global__ void k_import(DomDev D, const double* in, typename S::T* arena, const uint8_t* solid) {
     const int64_t n = (int64_t)D.nx * D.ny;
@@ -182,6 +215,13 @@ cudaError_t launch_fill_rest(int kind, const DomDev*, int ndom, const DomDev* hd
 cudaError_t launch_prime_mail(int kind, const DomDev& D, void* arena, const uint16_t* nflags, cudaStream_t s) {
     const int64_t nb = blocks_for((int64_t)D.nx * D.ny, 256);
     LBM_DISPATCH(kind, (k_prime_mail<S><<<(unsigned)nb, 256, 0, s>>>(D, static_cast<S::T*>(arena), nflags)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lj_wall(const DomDev& D, const uint8_t* solid, const LjEntry* tab, const int32_t* cnt, int dom,
+                           double2* out, cudaStream_t s) {
+    const int64_t nb = blocks_for((int64_t)D.nx * D.ny, 256);
+    k_lj_wall<<<(unsigned)nb, 256, 0, s>>>(D, solid, tab, cnt, dom, out);
     return cudaGetLastError();
 }
 

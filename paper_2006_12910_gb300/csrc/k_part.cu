@@ -161,10 +161,10 @@ __device__ __noinline__ int block_scan(int c, int* sh_warp, int& excl) {
     return total;
 }
 
-// Warps 3-7 of role A (160 threads) work as one group with their own named
-// barrier, so the other warps of the CTA never wait for them.
-constexpr int LJ_W0 = 3, LJ_NT = 160;
-__device__ __forceinline__ void lj_sync() { asm volatile("bar.sync 1, 160;" ::: "memory"); }
+// Warps 5-7 of role A (96 threads) prepare the LJ-type repulsion as one group
+// with their own named barrier, so the link and flip warps never wait for them.
+constexpr int LJ_W0 = 5, LJ_NT = 96;
+__device__ __forceinline__ void lj_sync() { asm volatile("bar.sync 1, 96;" ::: "memory"); }
 
 // Exclusive scan of small counts over the LJ group (gt = thread index in the
 // group); returns the group total.  sh holds one int per warp of the group.
@@ -200,43 +200,6 @@ constexpr int PB_CAP = 4096;   // nodes of a shared-memory inside bitmap
 constexpr int MAXNEAR = 64;     // nearby particles considered per particle
 
 
-// Other particles of the domain whose disks come within `extra` of the disk
-// (x, y, R), in index order, with their FP32 test data.  Every thread tests
-// its share of the particles; a block scan compacts the list, so the order is
-// fixed and no thread walks the particle array alone.
-__device__ __noinline__ void near_list(const PartArgs& a, const DomDev& D, int p, const PartState* states,
-                                          double x, double y, double R, double extra, int* list, DiskF* disks,
-                                          int* count, int* sh_warp) {
-    int total = 0;
-    for (int b0 = 0; b0 < D.np; b0 += PBLOCK) {
-        const int j = b0 + (int)threadIdx.x;
-        const int p2 = D.p0 + j;
-        int hit = 0;
-        PartState o;
-        double r2 = 0.0;
-        if (j < D.np && p2 != p) {
-            o = states[p2];
-            r2 = a.st[p2].R;
-            // FP32 centre distance with a one-node margin: a superset of the
-            // particles within reach is all that is needed here
-            float dx = (float)o.x - (float)x, dy = (float)o.y - (float)y;
-            if (D.flags & FLAG_PX) { const float L = (float)D.nx; dx -= L * rintf(dx / L); }
-            if (D.flags & FLAG_PY) { const float L = (float)D.ny; dy -= L * rintf(dy / L); }
-            const float reach = (float)(R + r2 + extra) + 1.0f;
-            hit = dx * dx + dy * dy <= reach * reach;
-        }
-        int excl;
-        const int tot = block_scan(hit, sh_warp, excl);
-        if (hit && total + excl < MAXNEAR) {
-            list[total + excl] = p2;
-            disks[total + excl] = make_diskf(o.x, o.y, r2);
-        }
-        total += tot;
-    }
-    if (threadIdx.x == 0) *count = total;
-    __syncthreads();
-}
-
 // Surface node of a disk (inside, with an 8-neighbour outside), unwrapped
 // coordinates near the disk, using the FP32 test with its exact fallback.
 __device__ __noinline__ bool is_surface_f(const DomDev& D, const DiskF& k, int x, int y) {
@@ -265,16 +228,16 @@ __device__ __forceinline__ void next_position(const DomDev& D, const PartState& 
 
 // Shared memory of one CTA; role A and role B use disjoint parts of a union.
 constexpr int NB_MAX = 4, NB_W = 32;  // inside bitmaps of up to 4 nearby disks, boxes up to 32 x 32
+constexpr int SURF_CAP = 1024;         // box nodes per LJ chunk, so at most this many surface nodes
 struct SmemA {
     double wsum[PBLOCK / 32][DIAG_N];  // per-warp partial sums
-    int16_t surf[LJ_NT];               // surface nodes of one chunk of the box (LJ group)
-    double2 arm[LJ_NT];                // their torque arms
-    int lj_any, lj_ns;
+    short2 sxy[SURF_CAP];              // surface nodes of one chunk of the box, relative to its corner (LJ group)
+    double2 arm[SURF_CAP];             // their torque arms
+    int lj_ns;
     int nb_h[NB_MAX];                  // half side of each nearby disk's bitmap (0: none)
     float nb_lim[MAXNEAR];             // reach of each nearby disk: R + r_it + 2
     uint8_t nbm[NB_MAX][NB_W * NB_W];  // inside tests of a nearby disk around its centre node
     uint8_t bm[PB_CAP];
-    uint8_t wall_win[PB_CAP];
     double lj_fx[LJ_TAB], lj_fy[LJ_TAB];
     int lj_ox[LJ_TAB], lj_oy[LJ_TAB];
 };
@@ -350,35 +313,6 @@ union SmemU {
     SmemB B;
 };
 
-// Status of every node of the box Bx, by nt threads (t = this thread's
-// index among them): 0 fluid, 1 solid, 2 beyond an open end, 3 beyond a y
-// wall.  Eight loads per thread are issued before any is used, so the solid
-// bytes arrive in one round trip instead of one per node.
-__device__ __forceinline__ void box_status(const DomDev& D, const uint8_t* solid, const Box& Bx, uint8_t* out, int t,
-                                           int nt) {
-    const int n = Bx.n();
-#pragma unroll 1
-    for (int base = 0; base < n; base += 8 * nt) {
-        uint8_t v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = base + u * nt + t;
-            v[u] = 2;
-            if (i < n) {
-                int x = Bx.x0 + i % Bx.w, y = Bx.y0 + i / Bx.w;
-                const bool ywall = (D.flags & FLAG_WY) && (y < 0 || y >= D.ny);
-                if (wrap_node(D, x, y)) v[u] = __ldg(solid + D.node_off + (int64_t)y * D.pitch + x) ? 1 : 0;
-                else v[u] = ywall ? 3 : 2;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = base + u * nt + t;
-            if (i < n) out[i] = v[u];
-        }
-    }
-}
-
 template <class S>
 __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes) {
     typedef typename S::A A;
@@ -394,7 +328,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
     if (blockIdx.x == 0 && threadIdx.x == 0 && advance) a.near_cnt[(t + 2) % 3] = 0;
     if (role == 0 ? !(modes & (PL_FORCES | PL_SWAP | PL_ADVANCE)) : !(modes & (role == 1 ? PL_RASTER : PL_MARK))) return;
     if (st.dom < 0) return;
-    const DomDev D = a.doms[a.one_domain ? 0 : st.dom];  // one domain: loaded without waiting for st
+    const DomDev D = a.one_domain ? a.dom0 : a.doms[st.dom];  // one domain: from the launch parameters
     if (p - D.p0 >= D.np) return;
     const int par = (int)(t & 1);
     const PartState* S0 = a.state + (int64_t)par * a.np;
@@ -434,10 +368,11 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
 
     if (role == 0) {
         // ------------------------------------------------------------------ role A
-        // Warps 0-1: the links, each with the force of Eq. MP1 and then the
+        // Warps 0-3: the links, each with the force of Eq. MP1 and then the
         // exchange of Eqs. MP7-MP8 on the same two slots (they belong to this
-        // link alone); warp 2: covered / uncovered nodes; warps 3-7: the
-        // LJ-type repulsion.  Each warp sums its own terms by shuffles in a
+        // link alone); warp 4: covered / uncovered nodes; warps 5-7: the
+        // set-up of the LJ-type repulsion, whose surface nodes all eight warps
+        // then share.  Each warp sums its own terms by shuffles in a
         // fixed order and thread 0 adds the warps up, so the totals are
         // deterministic and only the LJ group ever waits on a barrier of its
         // own before the final one.
@@ -450,21 +385,21 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
         double acc[DIAG_N];
 #pragma unroll
         for (int c = 0; c < DIAG_N; ++c) acc[c] = 0.0;
-        if (warp < 2) {
+        if (warp < 4) {
             // Eq. MP1: F = -2 [f'_k(r_v + e_k, t*) + rho0 omega_k (u_b . e_k) / c_s^2] e_k
             const A scl = (A)D.scale, inv = (A)D.inv_scale;
             if (forces || swap) {
                 // four links per thread at a time: all eight slot loads are in
                 // flight before any is used
 #pragma unroll 1
-                for (int l0 = threadIdx.x; l0 < nl; l0 += 4 * 64) {
+                for (int l0 = threadIdx.x; l0 < nl; l0 += 4 * 128) {
                     typename S::T* sa[4];
                     typename S::T* sb[4];
                     A va[4], vb[4];
                     int kk[4], vxs[4], vys[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int l = l0 + 64 * u;
+                        const int l = l0 + 128 * u;
                         const int32_t e = l < nl ? links[st.link_off + l] : 0;
                         const int node = e >> 3, k = (e & 7) + 1;
                         const int vy = node / D.pitch, vx = node - vy * D.pitch;
@@ -482,7 +417,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        if (l0 + 64 * u >= nl) break;
+                        if (l0 + 128 * u >= nl) break;
                         const int k = kk[u];
                         const double bx = min_image((vxs[u] + 0.5 * cx(k)) - q.x, D.nx, px);
                         const double by = min_image((vys[u] + 0.5 * cy(k)) - q.y, D.ny, py);
@@ -514,7 +449,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) sm.A.wsum[warp][c] = 0.0;
             }
-        } else if (warp == 2) {
+        } else if (warp == 4) {
             // Covered (+) / uncovered (-) nodes: F = +- rho (u - U_p), with rho and
             // sum f* e of the node at t written by the previous stream-collide pass.
             if (forces) {
@@ -542,14 +477,12 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
             for (int c = 3; c < DIAG_N; ++c) {
                 if (c >= 6 && c < 9) continue;
                 const double x = any ? warp_sum(acc[c]) : 0.0;
-                if (lane == 0) sm.A.wsum[2][c] = x;
+                if (lane == 0) sm.A.wsum[4][c] = x;
             }
         } else {
-            // Eq. MP2 between surface nodes of p and surface nodes of the other
-            // particles, and between surface nodes of p and stationary solid /
-            // wall nodes, within the threshold r_it.
+            // Eq. MP2 set-up: the other particles within reach, the pair-force
+            // table, the inside bitmap of this disk and those of nearby disks.
             const int gt = (int)threadIdx.x - LJ_W0 * 32;
-            bool on = false;
             if (forces && D.lj_psi != 0.0) {
                 // other particles within reach, in index order
                 if (gt == 0) nnear = 0;
@@ -578,168 +511,191 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
                 const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
                 const Box b = uni.bo;
                 const Box e = {b.x0 - 1, b.y0 - 1, b.w + 2, b.h + 2};
-                const int reach = (int)floor(D.lj_rit);
-                const bool use_bm = e.n() <= PB_CAP;
-                // 1 = wall or solid node within reach of the box, 0 = fluid or beyond an open end
-                const Box W = {b.x0 - reach, b.y0 - reach, b.w + 2 * reach, b.h + 2 * reach};
-                const bool use_win = W.n() <= PB_CAP;
-                if (gt == 0) sm.A.lj_any = 0;
-                if (use_win) box_status(D, a.solid, W, sm.A.wall_win, gt, LJ_NT);
-                lj_sync();
-                int any_wall = 0;
-                if (use_win) {
+                if (gt == 0) lj_n = a.lj_cnt[st.dom];
 #pragma unroll 1
-                    for (int i = gt; i < W.n(); i += LJ_NT) {
-                        const uint8_t st4 = sm.A.wall_win[i];
-                        const uint8_t v = (st4 == 1 || st4 == 3) ? 1 : 0;  // solid, or beyond a y wall
-                        sm.A.wall_win[i] = v;
-                        any_wall |= v;
+                for (int i = gt; i < LJ_TAB; i += LJ_NT) {
+                    const LjEntry en = a.lj_tab[(int64_t)st.dom * LJ_TAB + i];
+                    sm.A.lj_ox[i] = en.ox;
+                    sm.A.lj_oy[i] = en.oy;
+                    sm.A.lj_fx[i] = en.fx;
+                    sm.A.lj_fy[i] = en.fy;
+                }
+                if (e.n() <= PB_CAP) {
+                    const DiskF kf = uni.ko;
+#pragma unroll 1
+                    for (int i = gt; i < e.n(); i += LJ_NT)
+                        sm.A.bm[i] = inside_f(D, kf, e.x0 + i % e.w, e.y0 + i / e.w, false) ? 1 : 0;
+                }
+                // Inside bitmaps of the nearby disks (node offsets -h..h from
+                // the centre node, h = ceil(R) + 2, which holds every inside
+                // node and its neighbours): a surface test of theirs becomes
+                // shared-memory reads of the same FP32 / exact decisions.
+                if (gt < nn) sm.A.nb_lim[gt] = (float)(near_d[gt].R + D.lj_rit) + 2.0f;
+#pragma unroll 1
+                for (int j = 0; j < NB_MAX; ++j) {
+                    int h = 0;
+                    if (j < nn) {
+                        h = (int)ceilf((float)near_d[j].R) + 2;
+                        if (2 * h + 1 > NB_W) h = 0;
+                    }
+                    if (gt == 0) sm.A.nb_h[j] = h;
+                    const int side = 2 * h + 1;
+#pragma unroll 1
+                    for (int c = gt; h > 0 && c < side * side; c += LJ_NT) {
+                        const int ly = c / side, lx = c - ly * side;
+                        sm.A.nbm[j][ly * NB_W + lx] =
+                            inside_f(D, near_d[j], near_d[j].cx + lx - h, near_d[j].cy + ly - h, false) ? 1 : 0;
                     }
                 }
-                if (any_wall) sm.A.lj_any = 1;
-                lj_sync();
-                on = sm.A.lj_any != 0 || nn > 0 || !use_win;
-                if (on) {
-                    if (gt == 0) lj_n = a.lj_cnt[st.dom];
-#pragma unroll 1
-                    for (int i = gt; i < LJ_TAB; i += LJ_NT) {
-                        const LjEntry en = a.lj_tab[(int64_t)st.dom * LJ_TAB + i];
-                        sm.A.lj_ox[i] = en.ox;
-                        sm.A.lj_oy[i] = en.oy;
-                        sm.A.lj_fx[i] = en.fx;
-                        sm.A.lj_fy[i] = en.fy;
-                    }
-                    if (use_bm) {
-                        const DiskF kf = uni.ko;
-#pragma unroll 1
-                        for (int i = gt; i < e.n(); i += LJ_NT)
-                            sm.A.bm[i] = inside_f(D, kf, e.x0 + i % e.w, e.y0 + i / e.w, false) ? 1 : 0;
-                    }
-                    // Inside bitmaps of the nearby disks (node offsets -h..h from
-                    // the centre node, h = ceil(R) + 2, which holds every inside
-                    // node and its neighbours): a surface test of theirs becomes
-                    // shared-memory reads of the same FP32 / exact decisions.
-                    if (gt < nn) sm.A.nb_lim[gt] = (float)(near_d[gt].R + D.lj_rit) + 2.0f;
-#pragma unroll 1
-                    for (int j = 0; j < NB_MAX; ++j) {
-                        int h = 0;
-                        if (j < nn) {
-                            h = (int)ceilf((float)near_d[j].R) + 2;
-                            if (2 * h + 1 > NB_W) h = 0;
-                        }
-                        if (gt == 0) sm.A.nb_h[j] = h;
-                        const int side = 2 * h + 1;
-#pragma unroll 1
-                        for (int c = gt; h > 0 && c < side * side; c += LJ_NT) {
-                            const int ly = c / side, lx = c - ly * side;
-                            sm.A.nbm[j][ly * NB_W + lx] =
-                                inside_f(D, near_d[j], near_d[j].cx + lx - h, near_d[j].cy + ly - h, false) ? 1 : 0;
-                        }
-                    }
-                    lj_sync();
-                    const int ln = lj_n;
-                    // The box in chunks of LJ_NT nodes: compact the chunk's
-                    // surface nodes, then spread (surface node, offset) pairs
-                    // over the group.
-#pragma unroll 1
-                    for (int c0 = 0; c0 < b.n(); c0 += LJ_NT) {
-                        const int i = c0 + gt;
-                        bool surf = false;
-                        if (i < b.n()) {
-                            const int ay = b.y0 + i / b.w, ax = b.x0 + i % b.w;
-                            if (use_bm) {
-                                const int c = (ay - e.y0) * e.w + (ax - e.x0);
-                                surf = sm.A.bm[c] != 0;
-                                if (surf) {
-                                    bool all_in = true;
-#pragma unroll 1
-                                    for (int k = 1; k < 9; ++k) all_in &= sm.A.bm[c + cy(k) * e.w + cx(k)] != 0;
-                                    surf = !all_in;
-                                }
-                            } else {
-                                surf = is_surface(D, q.x, q.y, R, ax, ay);
-                            }
-                        }
-                        int excl;
-                        const int ns = lj_scan(surf ? 1 : 0, gt, sh_warp, excl);
-                        if (surf) {
-                            const int ay = b.y0 + i / b.w, ax = b.x0 + i % b.w;
-                            sm.A.surf[excl] = (int16_t)i;
-                            sm.A.arm[excl] = make_double2(min_image(ax - q.x, D.nx, px), min_image(ay - q.y, D.ny, py));
-                        }
-                        lj_sync();
-#pragma unroll 1
-                        for (int pi = gt; pi < ns * ln; pi += LJ_NT) {
-                            const int si = pi / ln, w = pi - si * ln;
-                            const int i2 = sm.A.surf[si];
-                            const int ay = b.y0 + i2 / b.w, ax = b.x0 + i2 % b.w;
-                            // wall / solid node at a + o_w
-                            int wx = ax + sm.A.lj_ox[w], wy = ay + sm.A.lj_oy[w];
-                            bool wall;
-                            if (use_win) {
-                                wall = sm.A.wall_win[(wy - W.y0) * W.w + (wx - W.x0)] != 0;
-                            } else if ((D.flags & FLAG_WY) && (wy < 0 || wy >= D.ny)) {
-                                wall = true;
-                            } else {
-                                wall = wrap_node(D, wx, wy) && a.solid[D.node_off + (int64_t)wy * D.pitch + wx] != 0;
-                            }
-                            int hits = wall ? 1 : 0;
-                            // surface nodes of the other particles at a + o_w
-#pragma unroll 1
-                            for (int j = 0; j < nn; ++j) {
-                                const DiskF& ko = near_d[j];
-                                const float ddx = (float)wrap_off(ax - ko.cx, D.nx, px) - ko.fx;
-                                const float ddy = (float)wrap_off(ay - ko.cy, D.ny, py) - ko.fy;
-                                const float lim = sm.A.nb_lim[j];
-                                if (ddx * ddx + ddy * ddy > lim * lim) continue;
-                                // node b = a + o expressed in the other particle's own frame
-                                const int ox = wrap_off(ax + sm.A.lj_ox[w] - ko.cx, D.nx, px);
-                                const int oy = wrap_off(ay + sm.A.lj_oy[w] - ko.cy, D.ny, py);
-                                const int h = j < NB_MAX ? sm.A.nb_h[j] : 0;
-                                bool surf_b;
-                                if (h > 0) {
-                                    surf_b = false;
-                                    if (ox > -h && ox < h && oy > -h && oy < h) {
-                                        const uint8_t* m = sm.A.nbm[j] + (oy + h) * NB_W + (ox + h);
-                                        if (*m) {
-                                            bool all_in = true;
-#pragma unroll 1
-                                            for (int k = 1; k < 9; ++k) all_in &= m[cy(k) * NB_W + cx(k)] != 0;
-                                            surf_b = !all_in;
-                                        }
-                                    }
-                                } else {
-                                    surf_b = is_surface_f(D, ko, ko.cx + ox, ko.cy + oy);
-                                }
-                                if (surf_b) ++hits;
-                            }
-                            if (hits) {
-                                const double rax = sm.A.arm[si].x, ray = sm.A.arm[si].y;
-                                const double fxw = sm.A.lj_fx[w] * hits, fyw = sm.A.lj_fy[w] * hits;
-                                acc[6] += fxw;
-                                acc[7] += fyw;
-                                acc[8] += rax * fyw - ray * fxw;
-                            }
-                        }
-                        lj_sync();
-                    }
-                }
-            }
-#pragma unroll
-            for (int c = 6; c < 9; ++c) {
-                const double x = on ? warp_sum(acc[c]) : 0.0;
-                if (lane == 0) sm.A.wsum[warp][c] = x;
             }
         }
         __syncthreads();
+        // Eq. MP2 over the surface nodes of p, by all eight warps: the force
+        // from static solid and wall nodes within r_it comes per node from the
+        // field precomputed with the geometry (the same table sum, taken once),
+        // the force from surface nodes of nearby particles pair by pair.
+        if (forces && D.lj_psi != 0.0) {
+            const int gt = threadIdx.x;
+            const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
+            const Box b = uni.bo;
+            const Box e = {b.x0 - 1, b.y0 - 1, b.w + 2, b.h + 2};
+            const bool use_bm = e.n() <= PB_CAP;
+            const int ln = lj_n;
+            const float inv_ln = ln > 0 ? 1.0f / (float)ln : 0.0f;
+#pragma unroll 1
+            for (int c0 = 0; c0 < b.n(); c0 += SURF_CAP) {
+                // each thread classifies a contiguous run (lattice order); one
+                // scan compacts the chunk's surface nodes with their torque arms
+                const int chn = min(SURF_CAP, b.n() - c0);
+                const int per = (chn + PBLOCK - 1) / PBLOCK;
+                const int i0 = c0 + gt * per, i1 = min(c0 + chn, i0 + per);
+                int ry = i0 / b.w, rx = i0 - ry * b.w;
+                uint32_t bits = 0;  // surface flags of this thread's run (per <= 4)
+#pragma unroll 1
+                for (int i = i0, k = 0; i < i1; ++i, ++k) {
+                    const int ay = b.y0 + ry, ax = b.x0 + rx;
+                    bool surf;
+                    if (use_bm) {
+                        const int c = (ay - e.y0) * e.w + (ax - e.x0);
+                        surf = sm.A.bm[c] != 0;
+                        if (surf) {
+                            bool all_in = true;
+#pragma unroll 1
+                            for (int kk = 1; kk < 9; ++kk) all_in &= sm.A.bm[c + cy(kk) * e.w + cx(kk)] != 0;
+                            surf = !all_in;
+                        }
+                    } else {
+                        surf = is_surface(D, q.x, q.y, R, ax, ay);
+                    }
+                    if (surf) bits |= 1u << k;
+                    if (++rx == b.w) { rx = 0; ++ry; }
+                }
+                int excl;
+                const int ns = block_scan(__popc(bits), sh_warp, excl);
+                ry = i0 / b.w;
+                rx = i0 - ry * b.w;
+#pragma unroll 1
+                for (int k = 0; bits >> k; ++k) {
+                    if ((bits >> k) & 1u) {
+                        int yy = ry, xx = rx + k;
+                        while (xx >= b.w) { xx -= b.w; ++yy; }
+                        sm.A.sxy[excl] = make_short2((short)xx, (short)yy);
+                        sm.A.arm[excl] = make_double2(min_image(b.x0 + xx - q.x, D.nx, px),
+                                                      min_image(b.y0 + yy - q.y, D.ny, py));
+                        ++excl;
+                    }
+                }
+                __syncthreads();
+                // static solids and walls: one field value per surface node
+#pragma unroll 1
+                for (int si = gt; si < ns; si += PBLOCK) {
+                    const short2 sp = sm.A.sxy[si];
+                    int ax = b.x0 + sp.x, ay = b.y0 + sp.y;
+                    double2 fw;
+                    if (wrap_node(D, ax, ay)) {
+                        fw = a.ljwall[D.node_off + (int64_t)ay * D.pitch + ax];
+                    } else {  // beyond an open end: the table sum on the spot
+                        fw = make_double2(0.0, 0.0);
+                        const int bx0 = b.x0 + sp.x, by0 = b.y0 + sp.y;
+#pragma unroll 1
+                        for (int j = 0; j < ln; ++j) {
+                            int wx = bx0 + sm.A.lj_ox[j], wy = by0 + sm.A.lj_oy[j];
+                            const bool wall = ((D.flags & FLAG_WY) && (wy < 0 || wy >= D.ny)) ||
+                                              (wrap_node(D, wx, wy) && a.solid[D.node_off + (int64_t)wy * D.pitch + wx] != 0);
+                            if (wall) { fw.x += sm.A.lj_fx[j]; fw.y += sm.A.lj_fy[j]; }
+                        }
+                    }
+                    if (fw.x != 0.0 || fw.y != 0.0) {
+                        const double rax = sm.A.arm[si].x, ray = sm.A.arm[si].y;
+                        acc[6] += fw.x;
+                        acc[7] += fw.y;
+                        acc[8] += rax * fw.y - ray * fw.x;
+                    }
+                }
+                // surface nodes of the other particles at a + o_w
+#pragma unroll 1
+                for (int pi = gt; nn > 0 && pi < ns * ln; pi += PBLOCK) {
+                    int si = (int)((float)pi * inv_ln);  // pi / ln, corrected below
+                    if (si * ln > pi) --si;
+                    else if ((si + 1) * ln <= pi) ++si;
+                    const int w = pi - si * ln;
+                    const short2 sp = sm.A.sxy[si];
+                    const int ax = b.x0 + sp.x, ay = b.y0 + sp.y;
+                    int hits = 0;
+#pragma unroll 1
+                    for (int j = 0; j < nn; ++j) {
+                        const DiskF& ko = near_d[j];
+                        const float ddx = (float)wrap_off(ax - ko.cx, D.nx, px) - ko.fx;
+                        const float ddy = (float)wrap_off(ay - ko.cy, D.ny, py) - ko.fy;
+                        const float lim = sm.A.nb_lim[j];
+                        if (ddx * ddx + ddy * ddy > lim * lim) continue;
+                        // node b = a + o expressed in the other particle's own frame
+                        const int ox = wrap_off(ax + sm.A.lj_ox[w] - ko.cx, D.nx, px);
+                        const int oy = wrap_off(ay + sm.A.lj_oy[w] - ko.cy, D.ny, py);
+                        const int h = j < NB_MAX ? sm.A.nb_h[j] : 0;
+                        bool surf_b;
+                        if (h > 0) {
+                            surf_b = false;
+                            if (ox > -h && ox < h && oy > -h && oy < h) {
+                                const uint8_t* m = sm.A.nbm[j] + (oy + h) * NB_W + (ox + h);
+                                if (*m) {
+                                    bool all_in = true;
+#pragma unroll 1
+                                    for (int kk = 1; kk < 9; ++kk) all_in &= m[cy(kk) * NB_W + cx(kk)] != 0;
+                                    surf_b = !all_in;
+                                }
+                            }
+                        } else {
+                            surf_b = is_surface_f(D, ko, ko.cx + ox, ko.cy + oy);
+                        }
+                        if (surf_b) ++hits;
+                    }
+                    if (hits) {
+                        const double rax = sm.A.arm[si].x, ray = sm.A.arm[si].y;
+                        const double fxw = sm.A.lj_fx[w] * hits, fyw = sm.A.lj_fy[w] * hits;
+                        acc[6] += fxw;
+                        acc[7] += fyw;
+                        acc[8] += rax * fyw - ray * fxw;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+#pragma unroll
+        for (int c = 6; c < 9; ++c) {
+            const double x = (forces && D.lj_psi != 0.0) ? warp_sum(acc[c]) : 0.0;
+            if (lane == 0) sm.A.wsum[warp][c] = x;
+        }
+        __syncthreads();
         if (forces && threadIdx.x < DIAG_N) {
-            // component groups: links 0-2 (warps 0-1), covered/uncovered 3-5 and
-            // 9-12 (warp 2), LJ 6-8 (warps 3-7); fixed order
+            // component groups: links 0-2 (warps 0-3), covered/uncovered 3-5 and
+            // 9-12 (warp 4), LJ 6-8 (all warps); fixed order
             const int c = threadIdx.x;
             double x = 0.0;
-            if (c < 3) x = sm.A.wsum[0][c] + sm.A.wsum[1][c];
-            else if (c < 6 || c >= 9) x = sm.A.wsum[2][c];
-            else x = (((sm.A.wsum[3][c] + sm.A.wsum[4][c]) + sm.A.wsum[5][c]) + sm.A.wsum[6][c]) + sm.A.wsum[7][c];
+            if (c < 3) x = ((sm.A.wsum[0][c] + sm.A.wsum[1][c]) + sm.A.wsum[2][c]) + sm.A.wsum[3][c];
+            else if (c < 6 || c >= 9) x = sm.A.wsum[4][c];
+            else
+                for (int w = 0; w < PBLOCK / 32; ++w) x += sm.A.wsum[w][c];
             tot[c] = x;
             a.diag[(int64_t)p * DIAG_N + c] = x;
         }
@@ -772,7 +728,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
         // Work items (row segments) within two nodes of the disk's boxes at t
         // and t+1 are "near": the stream-collide pass of that step runs them
         // after this kernel, and they hold every node that changes side.
-        const int mpar = (int)(t_next & 1);
+        const int mpar = (int)(t_next % 3);  // three-way: the passes of t and t+1 read the other two
         const int lpar = (int)(t_next % 3);
         const Box bo = uni.bo, bn = uni.bn;
         const int x0 = min(bo.x0, bn.x0) - 2, x1 = max(bo.x0 + bo.w, bn.x0 + bn.w) + 1;
@@ -801,16 +757,38 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
     // ---------------------------------------------------------------------- role B
 
     // Particles whose disks at t+1 may touch this one's: they bound the exterior
-    // nodes of the new links and reveal overlaps.
-    near_list(a, D, p, S0, q.x, q.y, R, 6.0, near, near_d, &nnear, sh_warp);
-    const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
-    if (nnear > MAXNEAR && threadIdx.x == 0) atomicOr(a.err, ERR_STATE);
-    if (threadIdx.x < nn) {
-        const int p2 = near[threadIdx.x];
-        const PartState o = S0[p2];
-        double ox = o.x, oy = o.y;
-        if (advance) next_position(D, o, a.st[p2].fixed, ox, oy);
-        near_d[threadIdx.x] = make_diskf(ox, oy, a.st[p2].R);
+    // nodes of the new links and reveal overlaps.  Warp 0 screens the
+    // domain's particles 32 at a time (ballots keep index order) and stores
+    // their disks at t+1.
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int total = 0;
+#pragma unroll 1
+        for (int b0 = 0; b0 < D.np; b0 += 32) {
+            const int j = b0 + lane, p2 = D.p0 + j;
+            bool hit = false;
+            PartState o;
+            if (j < D.np && p2 != p) {
+                o = S0[p2];
+                // FP32 centre distance with a one-node margin: a superset of the
+                // particles within reach is all that is needed here
+                float dx = (float)o.x - (float)q.x, dy = (float)o.y - (float)q.y;
+                if (px) { const float L = (float)D.nx; dx -= L * rintf(dx / L); }
+                if (py) { const float L = (float)D.ny; dy -= L * rintf(dy / L); }
+                const float reach = (float)(R + a.st[p2].R + 6.0) + 1.0f;
+                hit = dx * dx + dy * dy <= reach * reach;
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+            const int slot = total + __popc(bal & ((1u << lane) - 1u));
+            if (hit && slot < MAXNEAR) {
+                near[slot] = p2;
+                double ox = o.x, oy = o.y;
+                if (advance) next_position(D, o, a.st[p2].fixed, ox, oy);
+                near_d[slot] = make_diskf(ox, oy, a.st[p2].R);
+            }
+            total += __popc(bal);
+        }
+        if (lane == 0) nnear = total;
     }
     // Union of the old and new boxes; every neighbour of a node inside either
     // disk lies in it.
@@ -822,17 +800,43 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
     U.h = max(bo.y0 + bo.h, bn.y0 + bn.h) - U.y0;
     const bool use_bm = U.n() <= PB_CAP;
     if (use_bm) {
-        // 0 = fluid node in the domain, 1 = solid, 2 = outside the domain
-        box_status(D, a.solid, U, sm.B.node_st, threadIdx.x, PBLOCK);
+        // 0 = fluid node in the domain, 1 = solid, 2 = outside the domain;
+        // bnew / bold: inside the disk at t+1 / t.  Tiles of 32 columns x 32
+        // rows, warp w taking rows w, w + 8, w + 16, w + 24: no division, and
+        // four solid-byte loads per thread in flight at once.
         const DiskF kn = uni.kn, ko = uni.ko;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll 1
-        for (int i = threadIdx.x; i < U.n(); i += PBLOCK) {
-            const int xu = U.x0 + i % U.w, yu = U.y0 + i / U.w;
-            sm.B.bnew[i] = inside_f(D, kn, xu, yu, true) ? 1 : 0;
-            sm.B.bold[i] = advance ? (inside_f(D, ko, xu, yu, true) ? 1 : 0) : sm.B.bnew[i];
-            if (sm.B.node_st[i] == 3) sm.B.node_st[i] = 2;
+        for (int cb = 0; cb < U.w; cb += 32) {
+#pragma unroll 1
+            for (int rb = 0; rb < U.h; rb += 32) {
+                uint8_t stv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int r = rb + warp + 8 * u, cc = cb + lane;
+                    stv[u] = 2;
+                    if (r < U.h && cc < U.w) {
+                        int x = U.x0 + cc, y = U.y0 + r;
+                        if (wrap_node(D, x, y)) stv[u] = __ldg(a.solid + D.node_off + (int64_t)y * D.pitch + x) ? 1 : 0;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int r = rb + warp + 8 * u, cc = cb + lane;
+                    if (r < U.h && cc < U.w) {
+                        const int i = r * U.w + cc, xu = U.x0 + cc, yu = U.y0 + r;
+                        sm.B.node_st[i] = stv[u];
+                        const bool in_n = inside_f(D, kn, xu, yu, true);
+                        sm.B.bnew[i] = in_n ? 1 : 0;
+                        sm.B.bold[i] = advance ? (inside_f(D, ko, xu, yu, true) ? 1 : 0) : (in_n ? 1 : 0);
+                    }
+                }
+            }
         }
     }
+    __syncthreads();
+    const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
+    if (nnear > MAXNEAR && threadIdx.x == 0) atomicOr(a.err, ERR_STATE);
     __syncthreads();
     RastCtx rc;
     rc.D = a.doms + st.dom;

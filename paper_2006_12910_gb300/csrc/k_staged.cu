@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(STAGED_MAX_BLOCK) k_stream_staged(StreamArgs a
     const int64_t step64 = *a.ctr_in;
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.ctr_out = step64 + 1;
     const uint32_t step = (uint32_t)step64;
-    const int par = (int)(step64 & 1);
+    const int par = (int)(step64 % 3);
     const int32_t next_stamp = (int32_t)(step64 + 1);
     const bool far_only = a.mode == STREAM_FAR;
     const T* __restrict__ src = static_cast<const T*>(a.src);

@@ -32,9 +32,11 @@ __global__ void __launch_bounds__(512) k_stream_collide(StreamArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t step64 = *a.ctr_in;
-    if (a.mode != STREAM_NEAR && blockIdx.x == 0 && threadIdx.x == 0) *a.ctr_out = step64 + 1;
+    // every pass writes the (same) counter of the next state, so whichever
+    // pass a later kernel waits for has published it
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.ctr_out = step64 + 1;
     const uint32_t step = (uint32_t)step64;
-    const int par = (int)(step64 & 1);
+    const int par = (int)(step64 % 3);
     const T* __restrict__ src = static_cast<const T*>(a.src);
     T* __restrict__ dst = static_cast<T*>(a.dst);
     bool ok = true;

@@ -22,11 +22,11 @@ struct StreamArgs {
     int64_t* ctr_out;         // step counter of the destination state
     unsigned* err;            // sticky device error bits
     // Work selection: STREAM_ALL every item; STREAM_FAR the items not marked
-    // near a particle for this step (mark[step & 1][item] != step);
+    // near a particle for this step (mark[step % 3][item] != step);
     // STREAM_NEAR the items in near_list[step % 3][0 .. near_cnt[step % 3]).
     int mode;
     int flips;                // 1: also write the moments of tagged nodes (items near particles)
-    const int32_t* mark;      // [2][total_items]
+    const int32_t* mark;      // [3][total_items]
     const int32_t* near_list; // [3][total_items]
     const int32_t* near_cnt;  // [3]
     // Nodes that change side this step: a node whose tag carries step + 1
@@ -55,6 +55,11 @@ constexpr int STAGED_MAX_BLOCK = 256;
 // Rest state f* = omega_i rho0 on every fluid node of every domain.
 cudaError_t launch_fill_rest(int kind, const DomDev* doms, int ndom, const DomDev* hdoms, void* arena,
                              const uint8_t* solid, cudaStream_t s);
+// Per fluid node of one domain: the sum of the Eq. MP2 table forces of every
+// offset within r_it that lands on a solid node or beyond a y wall (node
+// offsets wrap on periodic axes; beyond an open end there is no wall).
+cudaError_t launch_lj_wall(const DomDev& D, const uint8_t* solid, const LjEntry* tab, const int32_t* cnt, int dom,
+                           double2* out, cudaStream_t s);
 // Mailbox bounce-back slots of one domain from its stored fluid populations
 // (after any write of the populations other than a step).
 cudaError_t launch_prime_mail(int kind, const DomDev& D, void* arena, const uint16_t* nflags, cudaStream_t s);
@@ -75,7 +80,8 @@ constexpr int CHECK_BLOCKS = 304;
 // ---- particle kernel (k_part.cu) ----
 struct PartArgs {
     const DomDev* doms;
-    int one_domain;            // 1 when the context has a single domain (its descriptor needs no lookup)
+    int one_domain;            // 1 when the context has a single domain: its descriptor is dom0
+    DomDev dom0;               // copy of doms[0] in the launch parameters (no dependent load)
     void* arena;               // populations holding f*(t) (read for forces, link slots exchanged)
     const uint8_t* solid;
     PartState* state;          // [2][np]: state at step t in slot (t & 1)
@@ -93,10 +99,11 @@ struct PartArgs {
     double* diag;              // np * DIAG_N
     unsigned* err;
     const int64_t* ctr;        // step counter of the state in `arena`
-    int32_t* mark;             // [2][total_items]
+    int32_t* mark;             // [3][total_items]
     int32_t* near_list;        // [3][total_items]
     int32_t* near_cnt;         // [3]
     int64_t total_items;
+    const double2* ljwall;     // per node: Eq. MP2 force from static solid / wall nodes within r_it (or null)
     const LjEntry* lj_tab;     // [ndom][LJ_TAB], valid entries first
     const int32_t* lj_cnt;     // [ndom]
 };
