@@ -200,6 +200,41 @@ constexpr int PB_CAP = 4096;   // nodes of a shared-memory inside bitmap
 constexpr int MAXNEAR = 64;     // nearby particles considered per particle
 
 
+// Inside nodes of one row yu of a disk, as the x range [x, y] (unwrapped; x > y
+// when the row misses the disk).  The disk's rows are convex and inside_f gives
+// the exact FP64 decision, so an estimate from the circle equation corrected by
+// a few inside_f tests at the ends yields exactly the nodes the per-node test
+// would accept.
+constexpr int RR_MAX = 64;  // rows of a box handled by ranges
+__device__ __noinline__ int2 row_range(const DomDev& D, const DiskF& k, int yu, bool wrapped) {
+    const int dyi = wrap_off(yu - k.cy, D.ny, D.flags & FLAG_PY);
+    const float dy = (float)dyi - k.fy;
+    const float s2 = (float)k.R * (float)k.R - dy * dy;
+    int xl, xr;
+    if (s2 >= 0.0f) {
+        const float sx = sqrtf(s2);
+        xl = k.cx + (int)ceilf(k.fx - sx);
+        xr = k.cx + (int)floorf(k.fx + sx);
+    } else {
+        xl = 1;
+        xr = 0;
+    }
+    if (xl > xr) {  // the estimate misses: the node nearest the centre decides
+        const int xc = k.cx + (k.fx >= 0.5f ? 1 : 0);
+        if (!inside_f(D, k, xc, yu, wrapped)) return make_int2(1, 0);
+        xl = xr = xc;
+    }
+#pragma unroll 1
+    while (inside_f(D, k, xl - 1, yu, wrapped)) --xl;
+#pragma unroll 1
+    while (xl <= xr && !inside_f(D, k, xl, yu, wrapped)) ++xl;
+#pragma unroll 1
+    while (inside_f(D, k, xr + 1, yu, wrapped)) ++xr;
+#pragma unroll 1
+    while (xr >= xl && !inside_f(D, k, xr, yu, wrapped)) --xr;
+    return make_int2(xl, xr);
+}
+
 // Surface node of a disk (inside, with an 8-neighbour outside), unwrapped
 // coordinates near the disk, using the FP32 test with its exact fallback.
 __device__ __noinline__ bool is_surface_f(const DomDev& D, const DiskF& k, int x, int y) {
@@ -234,6 +269,7 @@ struct SmemA {
     short2 sxy[SURF_CAP];              // surface nodes of one chunk of the box, relative to its corner (LJ group)
     double2 arm[SURF_CAP];             // their torque arms
     int lj_ns;
+    int2 rng[RR_MAX];                  // inside range of each row of the box (LJ surface list)
     int nb_h[NB_MAX];                  // half side of each nearby disk's bitmap (0: none)
     float nb_lim[MAXNEAR];             // reach of each nearby disk: R + r_it + 2
     uint8_t nbm[NB_MAX][NB_W * NB_W];  // inside tests of a nearby disk around its centre node
@@ -520,7 +556,10 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
                     sm.A.lj_fx[i] = en.fx;
                     sm.A.lj_fy[i] = en.fy;
                 }
-                if (e.n() <= PB_CAP) {
+                if (b.h <= RR_MAX) {
+#pragma unroll 1
+                    for (int r = gt; r < b.h; r += LJ_NT) sm.A.rng[r] = row_range(D, uni.ko, b.y0 + r, false);
+                } else if (e.n() <= PB_CAP) {
                     const DiskF kf = uni.ko;
 #pragma unroll 1
                     for (int i = gt; i < e.n(); i += LJ_NT)
@@ -562,8 +601,39 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
             const bool use_bm = e.n() <= PB_CAP;
             const int ln = lj_n;
             const float inv_ln = ln > 0 ? 1.0f / (float)ln : 0.0f;
+            const bool by_rows = b.h <= RR_MAX;
 #pragma unroll 1
-            for (int c0 = 0; c0 < b.n(); c0 += SURF_CAP) {
+            for (int c0 = 0; c0 < b.n(); c0 += (by_rows ? b.n() : SURF_CAP)) {
+              int ns;
+              if (by_rows) {
+                // surface nodes from the row ranges: a node of row y is interior
+                // when x-1..x+1 lie inside the ranges of rows y-1, y and y+1
+                int cnt = 0, il = 1, ir = 0;
+                int2 c = make_int2(1, 0);
+                if (gt < b.h) {
+                    c = sm.A.rng[gt];
+                    if (c.x <= c.y) {
+                        const int2 up = gt > 0 ? sm.A.rng[gt - 1] : make_int2(1, 0);
+                        const int2 dn = gt + 1 < b.h ? sm.A.rng[gt + 1] : make_int2(1, 0);
+                        if (up.x <= up.y && dn.x <= dn.y) {
+                            il = max(c.x, max(up.x, dn.x)) + 1;
+                            ir = min(c.y, min(up.y, dn.y)) - 1;
+                        }
+                        cnt = (c.y - c.x + 1) - (ir >= il ? ir - il + 1 : 0);
+                    }
+                }
+                int excl;
+                ns = block_scan(cnt, sh_warp, excl);
+#pragma unroll 1
+                for (int x = c.x; cnt > 0 && x <= c.y; ++x) {
+                    if (x >= il && x <= ir) continue;
+                    const int xx = x - b.x0;
+                    sm.A.sxy[excl] = make_short2((short)xx, (short)gt);
+                    sm.A.arm[excl] = make_double2(min_image(x - q.x, D.nx, px), min_image(b.y0 + gt - q.y, D.ny, py));
+                    ++excl;
+                }
+                __syncthreads();
+              } else {
                 // each thread classifies a contiguous run (lattice order); one
                 // scan compacts the chunk's surface nodes with their torque arms
                 const int chn = min(SURF_CAP, b.n() - c0);
@@ -591,7 +661,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
                     if (++rx == b.w) { rx = 0; ++ry; }
                 }
                 int excl;
-                const int ns = block_scan(__popc(bits), sh_warp, excl);
+                ns = block_scan(__popc(bits), sh_warp, excl);
                 ry = i0 / b.w;
                 rx = i0 - ry * b.w;
 #pragma unroll 1
@@ -606,6 +676,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
                     }
                 }
                 __syncthreads();
+              }
                 // static solids and walls: one field value per surface node
 #pragma unroll 1
                 for (int si = gt; si < ns; si += PBLOCK) {
