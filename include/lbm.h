@@ -183,7 +183,7 @@ int lbm_autotune(lbm_ctx* ctx, int trial_steps);
  * warp item per warp, 1 the same with a persistent grid-stride grid, 2 staged
  * through shared memory with bulk asynchronous copies (`stages` row segments
  * in flight per warp, 1..8; block at most 256 threads).  block: threads per
- * CTA, a multiple of 32 in [32, 512].  LBM_E_INVAL for values out of range
+ * CTA, a multiple of 32, at most 128 for kernels 0 and 1.  LBM_E_INVAL for values out of range
  * or a staged configuration whose shared memory does not fit an SM; the
  * previous configuration then stays.  lbm_get_launch writes {kernel, block,
  * stages, grid} to out4. */

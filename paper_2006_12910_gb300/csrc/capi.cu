@@ -89,8 +89,8 @@ struct lbm_ctx {
 
     int cur = 0;
     int64_t steps = 0;
-    int block = 256;
-    int grid_mode = 0;  // 0: one warp item per warp; 1: persistent grid-stride; 2: staged kernel
+    int block = 128;
+    int grid_mode = 1;  // 0: one warp item per warp; 1: persistent grid-stride; 2: staged kernel
     int stages = 0;     // row segments in flight per warp of the staged kernel
     int64_t grid = 1;
 
@@ -262,6 +262,10 @@ void build_flags(const DomDev& D, const uint8_t* solid, std::vector<uint16_t>& f
 
 int upload_geometry(lbm_ctx* c, int dom);
 
+// The NEAR pass always runs the register kernel, whose CTAs hold at most
+// REG_K1_MAX_BLOCK threads.
+int near_block(const lbm_ctx* c) { return std::min(c->block, REG_K1_MAX_BLOCK); }
+
 void set_launch(lbm_ctx* c) {
     const int64_t wpb = c->block / 32;
     int64_t full = (c->total_items + wpb - 1) / wpb;
@@ -290,7 +294,8 @@ void set_launch(lbm_ctx* c) {
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        c->near_grid = std::min<int64_t>(full, 2 * (int64_t)sms);
+        const int64_t nwpb = near_block(c) / 32;
+        c->near_grid = std::min<int64_t>((c->total_items + nwpb - 1) / nwpb, 2 * (int64_t)sms);
     }
     c->graph_dirty = true;
 }
@@ -366,7 +371,7 @@ cudaError_t enqueue_step(lbm_ctx* c, int cur, cudaStream_t s) {
     if ((e = cudaStreamWaitEvent(c->far_stream, c->ev_fork, 0)) != cudaSuccess) return e;
     if ((e = enqueue_stream_collide(c, cur, c->far_stream, c->block, c->grid, STREAM_FAR)) != cudaSuccess) return e;
     if ((e = launch_particle_step(c->kind, a, PL_STEP, s)) != cudaSuccess) return e;
-    if ((e = enqueue_stream_collide(c, cur, s, c->block, c->near_grid, STREAM_NEAR)) != cudaSuccess) return e;
+    if ((e = enqueue_stream_collide(c, cur, s, near_block(c), c->near_grid, STREAM_NEAR)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(c->ev_join, c->far_stream)) != cudaSuccess) return e;
     return cudaStreamWaitEvent(s, c->ev_join, 0);
 }
@@ -391,7 +396,7 @@ cudaError_t enqueue_graph_chains(lbm_ctx* c, int k, cudaStream_t s) {
         if ((e = cudaEventRecord(c->ev_far[st & 1], c->far_stream)) != cudaSuccess) return e;
         if ((e = launch_particle_step(c->kind, a, PL_STEP, s)) != cudaSuccess) return e;
         if (st > 0 && (e = cudaStreamWaitEvent(s, c->ev_far[(st - 1) & 1], 0)) != cudaSuccess) return e;
-        if ((e = enqueue_stream_collide(c, cur, s, c->block, c->near_grid, STREAM_NEAR)) != cudaSuccess) return e;
+        if ((e = enqueue_stream_collide(c, cur, s, near_block(c), c->near_grid, STREAM_NEAR)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(c->ev_near[st & 1], s)) != cudaSuccess) return e;
     }
     if ((e = cudaEventRecord(c->ev_join, c->far_stream)) != cudaSuccess) return e;
@@ -1123,8 +1128,10 @@ int lbm_autotune(lbm_ctx* c, int trial_steps) {
     // of which the next real step overwrites; the state f[cur] is read-only.
     struct Cand { int mode, block, stages; };
     std::vector<Cand> cands;
-    for (int mode = 0; mode < 2; ++mode)
-        for (int b : {128, 256, 512}) cands.push_back({mode, b, 0});
+    // the register kernel at 128 threads; fewer threads per CTA time faster
+    // alone but lose in the overlapped step (more CTAs to place beside the
+    // particle kernel)
+    for (int mode = 0; mode < 2; ++mode) cands.push_back({mode, 128, 0});
     for (Cand k : {Cand{2, 32, 1}, Cand{2, 64, 1}, Cand{2, 64, 2}, Cand{2, 128, 1}, Cand{2, 128, 2}, Cand{2, 256, 1}})
         if (staged_blocks_per_sm(c->kind, c->noise, c->pl, k.block, k.stages) > 0) cands.push_back(k);
     cudaEvent_t e0, e1;
@@ -1161,6 +1168,8 @@ int lbm_set_launch(lbm_ctx* c, int32_t kernel, int32_t block, int32_t stages) {
     if (!c) return LBM_E_INVAL;
     if (kernel < 0 || kernel > 2 || block < 32 || block > 512 || block % 32 != 0)
         return fail(c, LBM_E_INVAL, "kernel must be 0..2 and block a multiple of 32 in [32, 512]");
+    if (kernel < 2 && block > REG_K1_MAX_BLOCK)
+        return fail(c, LBM_E_INVAL, "the register kernel runs at most 128 threads per CTA");
     if (kernel == 2) {
         if (stages < 1 || stages > STAGED_MAX_STAGES || block > STAGED_MAX_BLOCK)
             return fail(c, LBM_E_INVAL, "staged kernel: stages 1..8 and block <= 256");

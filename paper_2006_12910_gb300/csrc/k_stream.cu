@@ -24,8 +24,16 @@
 
 namespace lbmk {
 
+// At most 128 threads per CTA.  The plain FP32 variants also ask for five
+// CTAs per SM: the compiler then keeps them at 96 registers (20 resident warps
+// per SM) without spilling, measured faster than 124-128 registers; noise and
+// power-law FP32 variants keep 128, FP64 and half-precision ones (twice the
+// values per lane or per node) up to 168.
+template <class S, bool NOISE, bool PL>
+constexpr int k1_min_blocks() { return S::V == 4 ? ((!NOISE && !PL) ? 5 : 4) : 3; }
+
 template <class S, bool NOISE, bool PL, bool FLIPS>
-__global__ void __launch_bounds__(512) k_stream_collide(StreamArgs a) {
+__global__ void __launch_bounds__(REG_K1_MAX_BLOCK, (k1_min_blocks<S, NOISE, PL>())) k_stream_collide(StreamArgs a) {
     typedef typename S::T T;
     typedef typename S::A A;
     constexpr int V = S::V;

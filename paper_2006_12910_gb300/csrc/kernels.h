@@ -48,6 +48,7 @@ int store_vector_width(int kind);
 // CTAs fit on one SM (0 when none does or the arguments are out of range).
 size_t staged_smem_bytes(int kind, int block, int stages);
 int staged_blocks_per_sm(int kind, bool noise, bool pl, int block, int stages);
+constexpr int REG_K1_MAX_BLOCK = 128;  // threads per CTA of the register kernel
 constexpr int STAGED_MAX_STAGES = 8;
 constexpr int STAGED_MAX_BLOCK = 256;
 

@@ -36,7 +36,7 @@ def twin(base, store, solid=None, particles=None, f0=None, launch=(2, 128, 3)):
     """Oracle, a context on the register kernel and one on the staged kernel."""
     ref, reg = pair(base, store, solid=solid, particles=particles, f0=f0)
     _, stg = pair(base, store, solid=solid, particles=particles, f0=f0)
-    reg.set_launch(0, 256, 0)
+    reg.set_launch(0, 128, 0)
     stg.set_launch(*launch)
     assert stg.launch()[:3] == tuple(launch)
     return ref, reg, stg
@@ -136,7 +136,7 @@ def test_staged_ensemble(store, errlog):
         plist.append(w.particles)
         f0s.append(f0)
     ctxs = []
-    for launch in [(0, 256, 0), (2, 128, 2)]:
+    for launch in [(0, 128, 0), (2, 128, 2)]:
         ctx = lbm.Context(ps, particles=plist)
         for d, f0 in enumerate(f0s):
             ctx.set_populations(f0, dom=d)
@@ -163,7 +163,7 @@ def test_staged_many_items_per_warp():
     rng = np.random.default_rng(5)
     f0 = (oracle.feq(1.0, 0.0, 0.0)[:, None, None] * (1 + 0.01 * rng.standard_normal((9, ny, nx)))).astype(np.float64)
     ctxs = []
-    for launch in [(0, 256, 0), (2, 64, 2)]:
+    for launch in [(1, 128, 0), (2, 64, 2)]:
         ctx = lbm.Context(gpu_params(base, "f32s", len(parts)), particles=[parts])
         ctx.set_populations(f0)
         ctx.set_launch(*launch)
@@ -180,7 +180,7 @@ def test_set_launch_rejects_bad_values():
     base = dict(nx=32, ny=32, periodic_x=1, periodic_y=1, walls_y=0, tau=0.8)
     ctx = lbm.Context(gpu_params(base, "f32s"))
     before = ctx.launch()
-    for bad in [(3, 128, 0), (0, 48, 0), (0, 1024, 0), (2, 128, 0), (2, 128, 9), (2, 512, 2), (-1, 128, 0)]:
+    for bad in [(3, 128, 0), (0, 48, 0), (0, 1024, 0), (1, 256, 0), (2, 128, 0), (2, 128, 9), (2, 512, 2), (-1, 128, 0)]:
         with pytest.raises(lbm.LbmError):
             ctx.set_launch(*bad)
         assert ctx.launch() == before
