@@ -191,11 +191,15 @@ int lbm_set_launch(lbm_ctx* ctx, int32_t kernel, int32_t block, int32_t stages);
 int lbm_get_launch(const lbm_ctx* ctx, int64_t* out4);
 
 /* Measurement: advance nsteps timesteps with plain launches in sequence (no
- * graph, no overlap) and a CUDA-event pair around every kernel on the
- * context stream; ms_out[0] receives the summed device time of the particle
- * kernel, ms_out[1] 0 (reserved), ms_out[2] that of the stream-and-collide
- * kernel over every work item, and launches_out (if not NULL) the number of
- * kernels launched.  Blocking.  The state advances exactly as with lbm_step. */
+ * graph, no overlap), enqueued back to back in batches of 32 steps with a
+ * CUDA-event pair around every kernel on the context stream and one
+ * synchronisation per batch; ms_out[0] receives the summed device time of
+ * the particle launch of forces, exchange and Newton-Euler, ms_out[1] that
+ * of the particle launches of rasterisation, marks and the Eq. MP2 sums
+ * (they run beside the stream-collide pass in lbm_step), ms_out[2] that of the
+ * stream-and-collide kernel over every work item, and launches_out (if not
+ * NULL) the number of kernels launched.  Blocking.  The state advances
+ * exactly as with lbm_step. */
 int lbm_profile_steps(lbm_ctx* ctx, int64_t nsteps, double* ms_out3, int64_t* launches_out);
 
 /* Largest row count lbm_checks_noalloc accepts (its static scratch holds one

@@ -49,6 +49,7 @@ struct lbm_ctx {
     uint32_t* special = nullptr;
     size_t special_words = 0;
     int64_t* ctr = nullptr;   // [2]
+    int64_t* pstep = nullptr; // [2]: by arena, the step after the last particle force launch from it
     unsigned* err = nullptr;  // sticky
     bool noise = false, pl = false;
 
@@ -71,20 +72,25 @@ struct lbm_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaStream_t side = nullptr;
     cudaStream_t far_stream = nullptr;   // branch running the far stream-collide items
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t rast_stream = nullptr;  // branch running the rasterisation of the next step
+    cudaStream_t lj_stream = nullptr;    // branch running the Eq. MP2 sums two steps ahead
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr, ev_join3 = nullptr;
+    cudaEvent_t ev_a[2] = {nullptr, nullptr}, ev_rast[2] = {nullptr, nullptr}, ev_lj[2] = {nullptr, nullptr};
     cudaEvent_t ev_far[2] = {nullptr, nullptr}, ev_near[2] = {nullptr, nullptr};  // per-step edges inside a graph
     bool overlap = true;                 // far items run concurrently with the particle kernels
     int32_t* mark = nullptr;             // [3][total_items]
     int32_t* near_list = nullptr;        // [3][total_items]
     int32_t* near_cnt = nullptr;         // [3]
-    int64_t* fliptag = nullptr;          // per node
+    int64_t* fliptag = nullptr;          // [2][nodes], copy by the parity of the tag's step
+    double* ljf = nullptr;               // [2][np_slots][4]: Eq. MP2 force and torque, copy by step parity
     double* flipmom = nullptr;           // [2][flips_total][3]
     int64_t near_grid = 1;
     LjEntry* lj_tab = nullptr;           // [ndom][LJ_TAB]
     double2* ljwall = nullptr;           // per node: Eq. MP2 force from walls / solids (domains with psi > 0)
     int32_t* lj_cnt = nullptr;           // [ndom]
     cudaEvent_t ev_snap = nullptr, ev_copied = nullptr;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // GRAPH_STEPS steps from state 0 / 1
+    cudaGraphExec_t gexec1[2] = {nullptr, nullptr};  // one step from state 0 / 1
     bool graph_dirty = true;
 
     int cur = 0;
@@ -100,6 +106,8 @@ struct lbm_ctx {
     double* d_sums = nullptr;
     float* d_mom = nullptr;
     float* h_mom = nullptr;
+    unsigned char* h_pin = nullptr;  // pinned: error word at 0, particle states from PIN_HEAD
+    size_t h_pin_bytes = 0;
     size_t mom_elems = 0;
     int mom_pending = 0;
 
@@ -310,6 +318,8 @@ PartArgs part_args(lbm_ctx* c, int cur) {
     a.state = c->pstate;
     a.flipmom = c->flipmom;
     a.fliptag = c->fliptag;
+    a.fliptag_stride = (int64_t)std::max<size_t>(1, c->node_bytes);
+    a.ljf = c->ljf;
     a.st = c->pst;
     a.np = c->np_slots;
     a.links = c->links;
@@ -321,6 +331,7 @@ PartArgs part_args(lbm_ctx* c, int cur) {
     a.diag = c->diag;
     a.err = c->err;
     a.ctr = c->ctr + cur;
+    a.pstep = c->pstep + cur;
     a.mark = c->mark;
     a.near_list = c->near_list;
     a.near_cnt = c->near_cnt;
@@ -352,90 +363,143 @@ cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int bloc
     a.near_list = c->near_list;
     a.near_cnt = c->near_cnt;
     a.fliptag = c->fliptag;
+    a.fliptag_stride = (int64_t)std::max<size_t>(1, c->node_bytes);
     a.flipmom = c->flipmom;
     return launch_stream_collide(c->kind, c->noise, c->pl, a, block, grid, c->grid_mode == 2 ? c->stages : 0, s);
 }
 
-// One timestep.  With particles the stream-collide items away from every
-// particle run on a second branch while the particle kernels and then the
-// near items run on the main branch; both branches join before the next step.
+// One timestep in sequence on one stream: with particles, the particle
+// launch of forces, exchange and Newton-Euler; the rasterisation and marks
+// for step t+1 and the Eq. MP2 sums for t+2 (they need the state of t+1
+// only); then the stream-collide pass over every item.
 cudaError_t enqueue_step(lbm_ctx* c, int cur, cudaStream_t s) {
     if (c->np_active == 0) return enqueue_stream_collide(c, cur, s, c->block, c->grid, STREAM_ALL);
     const PartArgs a = part_args(c, cur);
     cudaError_t e;
-    if (!c->overlap) {
-        if ((e = launch_particle_step(c->kind, a, PL_STEP, s)) != cudaSuccess) return e;
-        return enqueue_stream_collide(c, cur, s, c->block, c->grid, STREAM_ALL);
-    }
-    if ((e = cudaEventRecord(c->ev_fork, s)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(c->far_stream, c->ev_fork, 0)) != cudaSuccess) return e;
-    if ((e = enqueue_stream_collide(c, cur, c->far_stream, c->block, c->grid, STREAM_FAR)) != cudaSuccess) return e;
-    if ((e = launch_particle_step(c->kind, a, PL_STEP, s)) != cudaSuccess) return e;
-    if ((e = enqueue_stream_collide(c, cur, s, near_block(c), c->near_grid, STREAM_NEAR)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(c->ev_join, c->far_stream)) != cudaSuccess) return e;
-    return cudaStreamWaitEvent(s, c->ev_join, 0);
+    if ((e = launch_particle_step(c->kind, a, PL_STEP_A, s)) != cudaSuccess) return e;
+    if ((e = launch_particle_step(c->kind, a, PL_STEP_R, s)) != cudaSuccess) return e;
+    if ((e = launch_particle_step(c->kind, a, PL_STEP_LJ, s)) != cudaSuccess) return e;
+    return enqueue_stream_collide(c, cur, s, c->block, c->grid, STREAM_ALL);
 }
 
-// GRAPH_STEPS steps with particles, as two chains: on the main stream the
-// particle kernel and NEAR pass of every step, on the far stream the FAR
-// passes; FAR(t) waits only for NEAR(t-1) and NEAR(t) only for FAR(t-1).  So
-// the particle kernel of t+1 can start while FAR(t) is still running (it reads
-// and writes only slots near the particles, which NEAR(t) produced and FAR
-// never touches), and FAR(t+1) can start while the particle kernel of t+1
-// runs.  Marks are three-way and both passes publish the step counter, so no
-// kernel of one chain reads what a concurrent kernel of the other writes.
-cudaError_t enqueue_graph_chains(lbm_ctx* c, int k, cudaStream_t s) {
+// nsteps steps with particles, as four chains.  Main stream: the particle
+// launch of forces, exchange and Newton-Euler, and the NEAR pass of every
+// step.  Far stream: the FAR passes.  Raster stream: the rasterisation and
+// near-item marks for the following step, which need only the state that the
+// force launch wrote and so run beside the NEAR pass.  LJ stream: the Eq. MP2
+// sums two steps ahead.  Edges:
+//  - FAR(t) after NEAR(t-1): the near items of t-1 are the only ones it may
+//    read that the far chain did not write itself;
+//  - NEAR(t) after FAR(t-1) (it overwrites the arena FAR(t-1) read and reads
+//    its output at the seams) and after launch 2 for t (the node tags of
+//    side changes of t);
+//  - the rasterisation for t+1 after the force launch of t (state of t+1; the
+//    lists of t it replaces are read) and after FAR(t-1) (the marks it writes
+//    are the three-way copy FAR(t-1) read);
+//  - the Eq. MP2 sums for t+2 after the force launch of t (state of t+1; the
+//    sums of t they replace are read), and the force launch of t+2 after them.
+// The force launch of t+1 needs nothing from FAR(t): it reads and writes
+// only slots of items near the particles, which NEAR(t) produced.  What the
+// first steps of the graph need from launches of earlier steps ran before it
+// (previous graph or set-up).
+cudaError_t enqueue_graph_chains(lbm_ctx* c, int k, int nsteps, cudaStream_t s) {
     cudaError_t e;
     if ((e = cudaEventRecord(c->ev_fork, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(c->far_stream, c->ev_fork, 0)) != cudaSuccess) return e;
-    for (int st = 0; st < GRAPH_STEPS; ++st) {
+    if ((e = cudaStreamWaitEvent(c->rast_stream, c->ev_fork, 0)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c->lj_stream, c->ev_fork, 0)) != cudaSuccess) return e;
+    for (int st = 0; st < nsteps; ++st) {
         const int cur = k ^ (st & 1);
         const PartArgs a = part_args(c, cur);
         if (st > 0 && (e = cudaStreamWaitEvent(c->far_stream, c->ev_near[(st - 1) & 1], 0)) != cudaSuccess) return e;
         if ((e = enqueue_stream_collide(c, cur, c->far_stream, c->block, c->grid, STREAM_FAR)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(c->ev_far[st & 1], c->far_stream)) != cudaSuccess) return e;
-        if ((e = launch_particle_step(c->kind, a, PL_STEP, s)) != cudaSuccess) return e;
+        if (st > 1 && (e = cudaStreamWaitEvent(s, c->ev_lj[st & 1], 0)) != cudaSuccess) return e;  // sums of st
+        if ((e = launch_particle_step(c->kind, a, PL_STEP_A, s)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(c->ev_a[st & 1], s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(c->lj_stream, c->ev_a[st & 1], 0)) != cudaSuccess) return e;
+        if ((e = launch_particle_step(c->kind, a, PL_STEP_LJ, c->lj_stream)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(c->ev_lj[st & 1], c->lj_stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(c->rast_stream, c->ev_a[st & 1], 0)) != cudaSuccess) return e;
+        if (st > 0 && (e = cudaStreamWaitEvent(c->rast_stream, c->ev_far[(st - 1) & 1], 0)) != cudaSuccess) return e;
+        if ((e = launch_particle_step(c->kind, a, PL_STEP_R, c->rast_stream)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(c->ev_rast[st & 1], c->rast_stream)) != cudaSuccess) return e;
+        if (st > 0 && (e = cudaStreamWaitEvent(s, c->ev_rast[(st - 1) & 1], 0)) != cudaSuccess) return e;
         if (st > 0 && (e = cudaStreamWaitEvent(s, c->ev_far[(st - 1) & 1], 0)) != cudaSuccess) return e;
         if ((e = enqueue_stream_collide(c, cur, s, near_block(c), c->near_grid, STREAM_NEAR)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(c->ev_near[st & 1], s)) != cudaSuccess) return e;
     }
     if ((e = cudaEventRecord(c->ev_join, c->far_stream)) != cudaSuccess) return e;
-    return cudaStreamWaitEvent(s, c->ev_join, 0);
+    if ((e = cudaEventRecord(c->ev_join2, c->rast_stream)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(c->ev_join3, c->lj_stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, c->ev_join, 0)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, c->ev_join2, 0)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(s, c->ev_join3, 0);
+}
+
+// Captures nsteps steps starting from state k into one executable graph.
+int capture_steps(lbm_ctx* c, int k, int nsteps, cudaGraphExec_t* out) {
+    if (*out) { cudaGraphExecDestroy(*out); *out = nullptr; }
+    cudaGraph_t g = nullptr;
+    CKC(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    if (c->np_active > 0 && c->overlap) e = enqueue_graph_chains(c, k, nsteps, c->cap_stream);
+    else
+        for (int s = 0; s < nsteps && e == cudaSuccess; ++s) e = enqueue_step(c, k ^ (s & 1), c->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); CKC(c, e); }
+    CKC(c, e2);
+    e = cudaGraphInstantiate(out, g, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(g);
+    CKC(c, e);
+    return LBM_OK;
 }
 
 int build_graphs(lbm_ctx* c) {
     for (int k = 0; k < 2; ++k) {
-        if (c->gexec[k]) { cudaGraphExecDestroy(c->gexec[k]); c->gexec[k] = nullptr; }
-        cudaGraph_t g = nullptr;
-        CKC(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaSuccess;
-        if (c->np_active > 0 && c->overlap) e = enqueue_graph_chains(c, k, c->cap_stream);
-        else
-            for (int s = 0; s < GRAPH_STEPS && e == cudaSuccess; ++s) e = enqueue_step(c, k ^ (s & 1), c->cap_stream);
-        cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
-        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); CKC(c, e); }
-        CKC(c, e2);
-        e = cudaGraphInstantiate(&c->gexec[k], g, cudaGraphInstantiateFlagUseNodePriority);
-        cudaGraphDestroy(g);
-        CKC(c, e);
+        int r = capture_steps(c, k, GRAPH_STEPS, &c->gexec[k]);
+        if (!r) r = capture_steps(c, k, 1, &c->gexec1[k]);
+        if (r) return r;
     }
     c->graph_dirty = false;
     return LBM_OK;
 }
 
-int check_err(lbm_ctx* c) {
-    unsigned h = 0;
-    CKC(c, cudaMemcpy(&h, c->err, sizeof h, cudaMemcpyDeviceToHost));
+// Pinned host block: the error word in the first PIN_HEAD bytes, then
+// `extra` bytes of staging (the particle states).
+constexpr size_t PIN_HEAD = 64;
+int ensure_pin(lbm_ctx* c, size_t extra) {
+    if (c->h_pin_bytes >= PIN_HEAD + extra) return LBM_OK;
+    if (c->h_pin) cudaFreeHost(c->h_pin);
+    c->h_pin = nullptr;
+    c->h_pin_bytes = 0;
+    void* p = nullptr;
+    CKC(c, cudaMallocHost(&p, PIN_HEAD + extra));
+    c->h_pin = static_cast<unsigned char*>(p);
+    c->h_pin_bytes = PIN_HEAD + extra;
+    return LBM_OK;
+}
+
+int err_status(lbm_ctx* c, unsigned h) {
     if (h & ERR_UNSTABLE) return fail(c, LBM_E_UNSTABLE, "non-finite or non-positive density on the lattice");
     if (h & ERR_TIMEOUT) return fail(c, LBM_E_TIMEOUT, "a bounded device wait ran out");
     if (h & ERR_STATE) return fail(c, LBM_E_STATE, "particle overlap or particle list capacity exceeded");
     return LBM_OK;
 }
 
-int sync_and_check(lbm_ctx* c) {
-    CKC(c, cudaStreamSynchronize(c->stream));
-    return check_err(c);
+// Error word as of the work queued on stream s: one asynchronous copy into
+// pinned memory and one synchronisation.
+int check_err_on(lbm_ctx* c, cudaStream_t s) {
+    int r = ensure_pin(c, 0);
+    if (r) return r;
+    CKC(c, cudaMemcpyAsync(c->h_pin, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CKC(c, cudaStreamSynchronize(s));
+    return err_status(c, *reinterpret_cast<const volatile unsigned*>(c->h_pin));
 }
+
+int check_err(lbm_ctx* c) { return check_err_on(c, c->stream); }
+
+int sync_and_check(lbm_ctx* c) { return check_err_on(c, c->stream); }
 
 int ensure_stage(lbm_ctx* c, size_t bytes) {
     if (c->d_stage_bytes >= bytes) return LBM_OK;
@@ -476,9 +540,11 @@ int check_dom(lbm_ctx* c, int dom) {
 void free_particles(lbm_ctx* c) {
     cudaFree(c->pstate); cudaFree(c->pst); cudaFree(c->flipmom);
     cudaFree(c->links); cudaFree(c->nlinks); cudaFree(c->flips); cudaFree(c->nflips); cudaFree(c->diag);
+    cudaFree(c->ljf);
     c->pstate = nullptr; c->pst = nullptr; c->flipmom = nullptr;
     c->links = c->nlinks = c->flips = c->nflips = nullptr;
     c->diag = nullptr;
+    c->ljf = nullptr;
 }
 
 }  // namespace
@@ -557,21 +623,28 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
         // the particle chain is the critical path of an overlapped step: highest priority
         CKCR(cudaStreamCreateWithPriority(&c->cap_stream, cudaStreamNonBlocking, hi));
         CKCR(cudaStreamCreateWithPriority(&c->far_stream, cudaStreamNonBlocking, lo));
+        CKCR(cudaStreamCreateWithPriority(&c->rast_stream, cudaStreamNonBlocking, hi));
+        CKCR(cudaStreamCreateWithPriority(&c->lj_stream, cudaStreamNonBlocking, hi));
     }
     CKCR(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     CKCR(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     CKCR(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    CKCR(cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming));
+    CKCR(cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming));
     for (int k = 0; k < 2; ++k) {
         CKCR(cudaEventCreateWithFlags(&c->ev_far[k], cudaEventDisableTiming));
         CKCR(cudaEventCreateWithFlags(&c->ev_near[k], cudaEventDisableTiming));
+        CKCR(cudaEventCreateWithFlags(&c->ev_a[k], cudaEventDisableTiming));
+        CKCR(cudaEventCreateWithFlags(&c->ev_rast[k], cudaEventDisableTiming));
+        CKCR(cudaEventCreateWithFlags(&c->ev_lj[k], cudaEventDisableTiming));
     }
     CKCR(cudaMalloc(&c->mark, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items)));
     CKCR(cudaMalloc(&c->near_list, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items)));
     CKCR(cudaMalloc(&c->near_cnt, sizeof(int32_t) * 3));
     CKCR(cudaMemsetAsync(c->mark, 0xff, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items), c->stream));
     CKCR(cudaMemsetAsync(c->near_cnt, 0, sizeof(int32_t) * 3, c->stream));
-    CKCR(cudaMalloc(&c->fliptag, sizeof(int64_t) * std::max<size_t>(1, c->node_bytes)));
-    CKCR(cudaMemsetAsync(c->fliptag, 0xff, sizeof(int64_t) * std::max<size_t>(1, c->node_bytes), c->stream));
+    CKCR(cudaMalloc(&c->fliptag, sizeof(int64_t) * 2 * std::max<size_t>(1, c->node_bytes)));
+    CKCR(cudaMemsetAsync(c->fliptag, 0xff, sizeof(int64_t) * 2 * std::max<size_t>(1, c->node_bytes), c->stream));
     {
         // Eq. MP2 pair force per node offset within r_it, one table per domain
         std::vector<LjEntry> tab((size_t)ndom * LJ_TAB);
@@ -616,6 +689,8 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
     CKCR(cudaMalloc(&c->dd, sizeof(DomDev) * ndom));
     CKCR(cudaMalloc(&c->d_item_off, sizeof(int64_t) * ndom));
     CKCR(cudaMalloc(&c->ctr, sizeof(int64_t) * 2));
+    CKCR(cudaMalloc(&c->pstep, sizeof(int64_t) * 2));
+    CKCR(cudaMemsetAsync(c->pstep, 0, sizeof(int64_t) * 2, c->stream));
     CKCR(cudaMalloc(&c->err, sizeof(unsigned)));
     CKCR(cudaMalloc(&c->d_partial, sizeof(double) * 3 * CHECK_BLOCKS));
     CKCR(cudaMalloc(&c->d_sums, sizeof(double) * 3));
@@ -650,21 +725,31 @@ void lbm_destroy(lbm_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& g : c->gexec)
         if (g) cudaGraphExecDestroy(g);
+    for (auto& g : c->gexec1)
+        if (g) cudaGraphExecDestroy(g);
     cudaFree(c->f[0]); cudaFree(c->f[1]); cudaFree(c->solid); cudaFree(c->nflags); cudaFree(c->special);
-    cudaFree(c->dd); cudaFree(c->d_item_off); cudaFree(c->ctr); cudaFree(c->err);
+    cudaFree(c->dd); cudaFree(c->d_item_off); cudaFree(c->ctr); cudaFree(c->pstep); cudaFree(c->err);
     cudaFree(c->d_partial); cudaFree(c->d_sums); cudaFree(c->d_stage); cudaFree(c->d_mom);
     if (c->h_mom) cudaFreeHost(c->h_mom);
+    if (c->h_pin) cudaFreeHost(c->h_pin);
     free_particles(c);
     cudaFree(c->mark); cudaFree(c->near_list); cudaFree(c->near_cnt); cudaFree(c->lj_tab); cudaFree(c->lj_cnt);
     cudaFree(c->ljwall);
     cudaFree(c->fliptag);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_join2) cudaEventDestroy(c->ev_join2);
+    if (c->ev_join3) cudaEventDestroy(c->ev_join3);
     for (int k = 0; k < 2; ++k) {
         if (c->ev_far[k]) cudaEventDestroy(c->ev_far[k]);
         if (c->ev_near[k]) cudaEventDestroy(c->ev_near[k]);
+        if (c->ev_a[k]) cudaEventDestroy(c->ev_a[k]);
+        if (c->ev_rast[k]) cudaEventDestroy(c->ev_rast[k]);
+        if (c->ev_lj[k]) cudaEventDestroy(c->ev_lj[k]);
     }
     if (c->far_stream) cudaStreamDestroy(c->far_stream);
+    if (c->rast_stream) cudaStreamDestroy(c->rast_stream);
+    if (c->lj_stream) cudaStreamDestroy(c->lj_stream);
     if (c->ev_snap) cudaEventDestroy(c->ev_snap);
     if (c->ev_copied) cudaEventDestroy(c->ev_copied);
     if (c->side) cudaStreamDestroy(c->side);
@@ -755,6 +840,8 @@ int lbm_add_particles(lbm_ctx* c, int dom, int n, const lbm_particle* p) {
     CKC(c, cudaMalloc(&c->nlinks, sizeof(int32_t) * 2 * ns));
     CKC(c, cudaMalloc(&c->nflips, sizeof(int32_t) * 2 * ns));
     CKC(c, cudaMalloc(&c->diag, sizeof(double) * DIAG_N * ns));
+    CKC(c, cudaMalloc(&c->ljf, sizeof(double) * 2 * 4 * ns));
+    CKC(c, cudaMemset(c->ljf, 0, sizeof(double) * 2 * 4 * ns));
     CKC(c, cudaMemset(c->nlinks, 0, sizeof(int32_t) * 2 * ns));
     CKC(c, cudaMemset(c->nflips, 0, sizeof(int32_t) * 2 * ns));
     CKC(c, cudaMemset(c->diag, 0, sizeof(double) * DIAG_N * ns));
@@ -765,10 +852,15 @@ int lbm_add_particles(lbm_ctx* c, int dom, int n, const lbm_particle* p) {
     c->links_total = lo;
     c->flips_total = fo;
     // rasterise every particle at its current position (no link exchange, no
-    // flips) and mark the work items near the particles for the next step
+    // flips) and mark the work items near the particles for this step, then
+    // what every step expects to find: the rasterisation of the next step
+    // with its side changes and marks, and the Eq. MP2 sums of this step
     CKC(c, cudaMemsetAsync(c->mark, 0xff, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items), c->stream));
     CKC(c, cudaMemsetAsync(c->near_cnt, 0, sizeof(int32_t) * 3, c->stream));
     CKC(c, launch_particle_step(c->kind, part_args(c, c->cur), PL_RASTER | PL_MARK, c->stream));
+    CKC(c, launch_particle_step(c->kind, part_args(c, c->cur), PL_SETUP_R, c->stream));
+    CKC(c, launch_particle_step(c->kind, part_args(c, c->cur), PL_LJ, c->stream));
+    CKC(c, launch_particle_step(c->kind, part_args(c, c->cur), PL_LJ | PL_ADVANCE, c->stream));
     c->graph_dirty = true;
     return sync_and_check(c);
 }
@@ -814,7 +906,7 @@ int lbm_step(lbm_ctx* c, int64_t nsteps) {
         left -= GRAPH_STEPS;
     }
     while (left > 0) {
-        CKC(c, enqueue_step(c, c->cur, c->stream));
+        CKC(c, cudaGraphLaunch(c->gexec1[c->cur], c->stream));
         c->cur ^= 1;
         --left;
     }
@@ -889,7 +981,7 @@ int lbm_moments_async_wait(lbm_ctx* c, float* rho, float* ux, float* uy) {
     if (ux) memcpy(ux, c->h_mom + n, sizeof(float) * n);
     if (uy) memcpy(uy, c->h_mom + 2 * n, sizeof(float) * n);
     c->mom_pending = 0;
-    return check_err(c);
+    return check_err_on(c, c->side);
 }
 
 int lbm_particles(lbm_ctx* c, int dom, lbm_particle* out, int cap) {
@@ -897,9 +989,11 @@ int lbm_particles(lbm_ctx* c, int dom, lbm_particle* out, int cap) {
     if (r) return r;
     const DomDev& D = c->hd[dom];
     if (D.np == 0) return 0;
-    std::vector<PartState> s(D.np);
-    CKC(c, cudaMemcpyAsync(s.data(), c->pstate + (c->steps & 1) * c->np_slots + D.p0, sizeof(PartState) * D.np,
-                           cudaMemcpyDeviceToHost, c->stream));
+    r = ensure_pin(c, sizeof(PartState) * (size_t)D.np);
+    if (r) return r;
+    const PartState* s = reinterpret_cast<const PartState*>(c->h_pin + PIN_HEAD);
+    CKC(c, cudaMemcpyAsync(c->h_pin + PIN_HEAD, c->pstate + (c->steps & 1) * c->np_slots + D.p0,
+                           sizeof(PartState) * D.np, cudaMemcpyDeviceToHost, c->stream));
     r = sync_and_check(c);
     if (r) return r;
     for (int i = 0; i < D.np && i < cap && out; ++i) {
@@ -1055,6 +1149,8 @@ int lbm_load(lbm_ctx* c, const char* path) {
         CKC(c, cudaMalloc(&c->nflips, 2 * 4 * ns));
         const int64_t pr = h.steps & 1;  // the lists of the restored step
         CKC(c, cudaMalloc(&c->diag, 8 * ns * DIAG_N));
+        CKC(c, cudaMalloc(&c->ljf, sizeof(double) * 2 * 4 * ns));
+        CKC(c, cudaMemset(c->ljf, 0, sizeof(double) * 2 * 4 * ns));
         CKC(c, cudaMemcpy(c->pstate, s.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
         CKC(c, cudaMemcpy(c->pstate + ns, s.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
         CKC(c, cudaMemcpy(c->flipmom + pr * fm.size(), fm.data(), 8 * fm.size(), cudaMemcpyHostToDevice));
@@ -1072,6 +1168,9 @@ int lbm_load(lbm_ctx* c, const char* path) {
         CKC(c, cudaMemset(c->mark, 0xff, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items)));
         CKC(c, cudaMemset(c->near_cnt, 0, sizeof(int32_t) * 3));
         CKC(c, launch_particle_step(c->kind, part_args(c, c->cur), PL_MARK, c->stream));
+        CKC(c, launch_particle_step(c->kind, part_args(c, c->cur), PL_SETUP_R, c->stream));
+        CKC(c, launch_particle_step(c->kind, part_args(c, c->cur), PL_LJ, c->stream));
+        CKC(c, launch_particle_step(c->kind, part_args(c, c->cur), PL_LJ | PL_ADVANCE, c->stream));
         CKC(c, cudaStreamSynchronize(c->stream));
     }
     CKC(c, cudaMemcpy(c->dd, c->hd.data(), sizeof(DomDev) * c->ndom, cudaMemcpyHostToDevice));
@@ -1084,36 +1183,66 @@ int lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double* ms_out3, int64_t* laun
     if (!c || !ms_out3 || nsteps < 0) return c ? fail(c, LBM_E_INVAL, "bad arguments") : LBM_E_INVAL;
     int r = sync_and_check(c);
     if (r) return r;
-    const int NE = 6;
-    cudaEvent_t ev[NE];
-    for (int k = 0; k < NE; ++k) CKC(c, cudaEventCreate(&ev[k]));
+    // Steps are enqueued back to back in batches, an event pair around every
+    // kernel and one synchronisation per batch, so that each pair brackets
+    // one kernel of a busy stream and no host launch latency.
+    const int BATCH = 32, NE = 6 * BATCH;
+    std::vector<cudaEvent_t> ev(NE, nullptr);
+    for (auto& e : ev) {
+        cudaError_t ce = cudaEventCreate(&e);
+        if (ce != cudaSuccess) {
+            for (auto& x : ev)
+                if (x) cudaEventDestroy(x);
+            CKC(c, ce);
+        }
+    }
+    auto destroy = [&]() {
+        for (auto& x : ev) cudaEventDestroy(x);
+    };
     double acc[3] = {0.0, 0.0, 0.0};
     int64_t launches = 0;
-    for (int64_t s = 0; s < nsteps; ++s) {
-        const bool parts = c->np_active > 0;
-        if (parts) {
-            const PartArgs a = part_args(c, c->cur);
-            CKC(c, cudaEventRecord(ev[0], c->stream));
-            CKC(c, launch_particle_step(c->kind, a, PL_STEP, c->stream));
-            CKC(c, cudaEventRecord(ev[1], c->stream));
+    const bool parts = c->np_active > 0;
+    for (int64_t s0 = 0; s0 < nsteps; s0 += BATCH) {
+        const int nb = (int)std::min<int64_t>(BATCH, nsteps - s0);
+        cudaError_t ce = cudaSuccess;
+        for (int b = 0; b < nb && ce == cudaSuccess; ++b) {
+            cudaEvent_t* e = ev.data() + 6 * b;
+            if (parts) {
+                const PartArgs a = part_args(c, c->cur);
+                if (ce == cudaSuccess) ce = cudaEventRecord(e[0], c->stream);
+                if (ce == cudaSuccess) ce = launch_particle_step(c->kind, a, PL_STEP_A, c->stream);
+                if (ce == cudaSuccess) ce = cudaEventRecord(e[1], c->stream);
+                if (ce == cudaSuccess) ce = launch_particle_step(c->kind, a, PL_STEP_R, c->stream);
+                if (ce == cudaSuccess) ce = launch_particle_step(c->kind, a, PL_STEP_LJ, c->stream);
+                if (ce == cudaSuccess) ce = cudaEventRecord(e[4], c->stream);
+                launches += 3;
+            }
+            if (ce == cudaSuccess) ce = cudaEventRecord(e[2], c->stream);
+            if (ce == cudaSuccess) ce = enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e[3], c->stream);
             launches += 1;
+            c->cur ^= 1;
+            c->steps += 1;
         }
-        CKC(c, cudaEventRecord(ev[3], c->stream));
-        CKC(c, enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid));
-        CKC(c, cudaEventRecord(ev[4], c->stream));
-        launches += 1;
-        CKC(c, cudaEventSynchronize(ev[4]));
-        float ms = 0.f;
-        if (parts) {
-            CKC(c, cudaEventElapsedTime(&ms, ev[0], ev[1]));
-            acc[0] += ms;
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+        for (int b = 0; b < nb && ce == cudaSuccess; ++b) {
+            cudaEvent_t* e = ev.data() + 6 * b;
+            float ms = 0.f;
+            if (parts) {
+                ce = cudaEventElapsedTime(&ms, e[0], e[1]);
+                acc[0] += ms;
+                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e[1], e[4]);
+                acc[1] += ms;
+            }
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e[2], e[3]);
+            acc[2] += ms;
         }
-        CKC(c, cudaEventElapsedTime(&ms, ev[3], ev[4]));
-        acc[2] += ms;
-        c->cur ^= 1;
-        c->steps += 1;
+        if (ce != cudaSuccess) {
+            destroy();
+            CKC(c, ce);
+        }
     }
-    for (int k = 0; k < NE; ++k) cudaEventDestroy(ev[k]);
+    destroy();
     for (int k = 0; k < 3; ++k) ms_out3[k] = acc[k];
     if (launches_out) *launches_out = launches;
     return check_err(c);

@@ -1,26 +1,31 @@
 // k_part.cu -- particle kernel of the D2Q9 hot path (arXiv:2006.12910 Sec. 3).
 //
-// One launch per timestep with three CTAs per particle that run side by side
-// (roles A, B and C below).  The stored populations are f*(t),
-// post-collision; the particle state and the link / flip lists are
-// double-buffered by the parity of the step, so A reads the lists of t while
-// B writes those of t+1.  Role A (phases 1-2), role B (phase 3) and role C
-// (phase 4):
-//  1. forces at t: Eq. MP1 over the boundary links of the rasterisation at t
-//     (each link's slots belong to this particle alone), the covered /
-//     uncovered-node force of Eq. MP3 from the node moments that the
-//     stream-collide pass of the previous step wrote while producing f*(t),
-//     and the LJ-type repulsion of Eq. MP2; FP64 totals (Eqs. MP3-MP4) and the
-//     Newton-Euler update of Eqs. MP5-MP6;
-//  2. Eqs. MP7-MP8 as a pre-stream exchange: for the link r_v -> r_v + e_k the
-//     slot that r_v + e_k pulls next receives f*_{-k}(r_v + e_k) +
-//     2 rho0 omega_k (u_b . e_k) / c_s^2 and the slot r_v pulls receives
-//     f*_k(r_v) minus the same, so the plain pull stream realises the moving
-//     bounce-back on both sides;
-//  3. re-rasterisation at r_c(t+1) = r_c(t) + U_p(t), which needs no force and
-//     therefore no other CTA's result: new link list and the nodes that change
-//     side (tagged for the next stream-collide pass);
-//  4. the work items near the particle for the next step.
+// Three launches per timestep, each with CTAs per particle in roles that
+// run side by side.  The stored populations are f*(t), post-collision; the
+// particle state, the link / flip lists, the node tags of side changes and
+// the Eq. MP2 sums are double-buffered by the parity of the step they belong
+// to, so a launch reads the copies of one step while it writes those of
+// another.
+//
+//  A. (launch 1 of step t) forces at t: Eq. MP1 over the boundary links of
+//     the rasterisation at t (each link's slots belong to this particle
+//     alone) and the covered / uncovered-node force of Eq. MP3 from the node
+//     moments that the stream-collide pass of the previous step wrote while
+//     producing f*(t), plus the Eq. MP2 force at t summed two steps earlier;
+//     FP64 totals (Eqs. MP3-MP4) and the Newton-Euler update of Eqs. MP5-MP6.
+//     With the forces, Eqs. MP7-MP8 as a pre-stream exchange: for the link
+//     r_v -> r_v + e_k the slot that r_v + e_k pulls next receives
+//     f*_{-k}(r_v + e_k) + 2 rho0 omega_k (u_b . e_k) / c_s^2 and the slot r_v
+//     pulls receives f*_k(r_v) minus the same, so the plain pull stream
+//     realises the moving bounce-back on both sides.
+// After launch 1 of step t has written the state of t+1, beside the
+// stream-collide pass of step t:
+//  B, C. (launch 2) for step t+1: re-rasterisation at r_c(t+2) = r_c(t+1) +
+//     U_p(t+1), which needs no force of t+1 (new link list and the nodes that
+//     change side, tagged for the stream-collide pass of t+1), and the work
+//     items near the particle for step t+2;
+//  D. (launch 3) Eq. MP2 at t+2, which needs positions only.
+// At set-up the same roles run for the current step.
 #include "kernels.h"
 #include "lbm_dev.cuh"
 
@@ -261,7 +266,7 @@ __device__ __forceinline__ void next_position(const DomDev& D, const PartState& 
     if (D.flags & FLAG_PY) y = wrap_coord(y, D.ny);
 }
 
-// Shared memory of one CTA; role A and role B use disjoint parts of a union.
+// Shared memory of one CTA; roles A / D and role B use disjoint parts of a union.
 constexpr int NB_MAX = 4, NB_W = 32;  // inside bitmaps of up to 4 nearby disks, boxes up to 32 x 32
 constexpr int SURF_CAP = 1024;         // box nodes per LJ chunk, so at most this many surface nodes
 struct SmemA {
@@ -350,19 +355,28 @@ union SmemU {
 };
 
 template <class S>
-__global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes) {
+__global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes, int role0) {
     typedef typename S::A A;
-    const int role = (int)blockIdx.x / a.np;  // 0: forces and exchange, 1: rasterisation, 2: near-item marks
-    const int p = (int)blockIdx.x - role * a.np;
+    // 0: forces, exchange and Newton-Euler; 1: Eq. MP2 for the next step;
+    // 2: rasterisation; 3: near-item marks
+    const int rel = (int)blockIdx.x / a.np;
+    const int role = role0 + rel;
+    const int p = (int)blockIdx.x - rel * a.np;
     // Independent loads first (step counter, static data, both parities of
     // the state), so the prologue waits for one round trip, then the domain.
-    const int64_t t = *a.ctr;
+    // PL_AHEAD: launched after role A of step t-1 for step t (or t+1), whose
+    // state counter is not yet published: t from the word role A stored.
+    const int64_t t = (modes & PL_AHEAD) ? *a.pstep : *a.ctr;
     const PartStatic st = a.st[p];
     const PartState q0 = a.state[p], q1 = a.state[(int64_t)a.np + p];
     const bool advance = modes & PL_ADVANCE;
     // The near-item list of step t+2 is touched by nobody during this step.
-    if (blockIdx.x == 0 && threadIdx.x == 0 && advance) a.near_cnt[(t + 2) % 3] = 0;
-    if (role == 0 ? !(modes & (PL_FORCES | PL_SWAP | PL_ADVANCE)) : !(modes & (role == 1 ? PL_RASTER : PL_MARK))) return;
+    if (role == 0 && p == 0 && threadIdx.x == 0 && advance) {
+        a.near_cnt[(t + 2) % 3] = 0;
+        *a.pstep = t + 1;
+    }
+    const int need = role == 0 ? (PL_FORCES | PL_SWAP) : role == 1 ? PL_LJ : role == 2 ? PL_RASTER : PL_MARK;
+    if (!(modes & need)) return;
     if (st.dom < 0) return;
     const DomDev D = a.one_domain ? a.dom0 : a.doms[st.dom];  // one domain: from the launch parameters
     if (p - D.p0 >= D.np) return;
@@ -406,12 +420,10 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
         // ------------------------------------------------------------------ role A
         // Warps 0-3: the links, each with the force of Eq. MP1 and then the
         // exchange of Eqs. MP7-MP8 on the same two slots (they belong to this
-        // link alone); warp 4: covered / uncovered nodes; warps 5-7: the
-        // set-up of the LJ-type repulsion, whose surface nodes all eight warps
-        // then share.  Each warp sums its own terms by shuffles in a
-        // fixed order and thread 0 adds the warps up, so the totals are
-        // deterministic and only the LJ group ever waits on a barrier of its
-        // own before the final one.
+        // link alone); warp 4: covered / uncovered nodes.  The Eq. MP2 force
+        // at t was summed by role D two steps earlier (or at set-up).
+        // Each warp sums its own terms by shuffles in a fixed order and the
+        // warps are added in a fixed order, so the totals are deterministic.
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const int32_t* links = a.links + (int64_t)par * a.links_total;
         const int32_t* flips = a.flips + (int64_t)par * a.flips_total;
@@ -515,20 +527,75 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
                 const double x = any ? warp_sum(acc[c]) : 0.0;
                 if (lane == 0) sm.A.wsum[4][c] = x;
             }
-        } else {
-            // Eq. MP2 set-up: the other particles within reach, the pair-force
+        }
+        __syncthreads();
+        if (forces && threadIdx.x < DIAG_N) {
+            // component groups: links 0-2 (warps 0-3), covered/uncovered 3-5 and
+            // 9-12 (warp 4), LJ 6-8 (role D, earlier launch); fixed order
+            const int c = threadIdx.x;
+            double x = 0.0;
+            if (c < 3) x = ((sm.A.wsum[0][c] + sm.A.wsum[1][c]) + sm.A.wsum[2][c]) + sm.A.wsum[3][c];
+            else if (c < 6 || c >= 9) x = sm.A.wsum[4][c];
+            else if (D.lj_psi != 0.0) x = a.ljf[4 * ((int64_t)par * a.np + p) + (c - 6)];
+            tot[c] = x;
+            a.diag[(int64_t)p * DIAG_N + c] = x;
+        }
+        __syncthreads();
+        if (advance && threadIdx.x == 0) {
+            // Eqs. MP5, MP6 (velocities) with r_c(t+1) = r_c(t) + U_p(t).
+            PartState n = q;
+            if (!st.fixed) {
+                if (forces) {
+                    const double Fx = (tot[0] + tot[3]) + tot[6], Fy = (tot[1] + tot[4]) + tot[7];
+                    const double T = (tot[2] + tot[5]) + tot[8];
+                    n.U = q.U + Fx * st.inv_m + st.buoy * D.gx;
+                    n.V = q.V + Fy * st.inv_m + st.buoy * D.gy;
+                    n.Om = q.Om + T * st.inv_I;
+                }
+                n.x = nxp;
+                n.y = nyp;
+                n.th = q.th + q.Om;
+                if (fabs(q.U) >= 1.0 || fabs(q.V) >= 1.0) atomicOr(a.err, ERR_STATE);  // faster than a node per step
+            }
+            a.state[(int64_t)(par ^ 1) * a.np + p] = n;
+        }
+        return;
+    }
+
+    if (role == 1) {
+        // ------------------------------------------------------------------ role D
+        // Eq. MP2 on p at the step this launch advances to (t+1, or t
+        // without PL_ADVANCE): it needs only positions, and r_c(t+1) =
+        // r_c(t) + U_p(t) is known before the forces at t are, so the sum
+        // runs off the path of the force and exchange launches.  Warps 5-7
+        // prepare (their own named barrier), then all eight warps take the
+        // surface nodes; fixed-order sums into ljf[(t+1) & 1].
+        if (!(D.lj_psi != 0.0)) return;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const DiskF kd = uni.kn;  // the disk at the target step
+        const Box bd = uni.bn;
+        const double cxd = nxp, cyd = nyp;
+        double acc[DIAG_N];
+#pragma unroll
+        for (int c = 0; c < DIAG_N; ++c) acc[c] = 0.0;
+        if (warp >= LJ_W0) {
+            // Set-up: the other particles within reach, the pair-force
             // table, the inside bitmap of this disk and those of nearby disks.
             const int gt = (int)threadIdx.x - LJ_W0 * 32;
-            if (forces && D.lj_psi != 0.0) {
+            {
                 // other particles within reach, in index order
                 if (gt == 0) nnear = 0;
                 lj_sync();
                 for (int b0 = 0; b0 < D.np; b0 += LJ_NT) {
                     const int j = b0 + gt, p2 = D.p0 + j;
                     int hit = 0;
+                    double ox = 0.0, oy = 0.0;
                     if (j < D.np && p2 != p) {
                         const PartState o = S0[p2];
-                        float dx = (float)o.x - (float)q.x, dy = (float)o.y - (float)q.y;
+                        ox = o.x;
+                        oy = o.y;
+                        if (advance) next_position(D, o, a.st[p2].fixed, ox, oy);
+                        float dx = (float)ox - (float)cxd, dy = (float)oy - (float)cyd;
                         if (px) { const float L = (float)D.nx; dx -= L * rintf(dx / L); }
                         if (py) { const float L = (float)D.ny; dy -= L * rintf(dy / L); }
                         const float reach = (float)(R + a.st[p2].R + D.lj_rit + 4.0) + 1.0f;
@@ -538,14 +605,14 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
                     const int tot_hit = lj_scan(hit, gt, sh_warp, excl);
                     if (hit && nnear + excl < MAXNEAR) {
                         near[nnear + excl] = p2;
-                        near_d[nnear + excl] = make_diskf(S0[p2].x, S0[p2].y, a.st[p2].R);
+                        near_d[nnear + excl] = make_diskf(ox, oy, a.st[p2].R);
                     }
                     lj_sync();
                     if (gt == 0) nnear += tot_hit;
                     lj_sync();
                 }
                 const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
-                const Box b = uni.bo;
+                const Box b = bd;
                 const Box e = {b.x0 - 1, b.y0 - 1, b.w + 2, b.h + 2};
                 if (gt == 0) lj_n = a.lj_cnt[st.dom];
 #pragma unroll 1
@@ -558,9 +625,9 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
                 }
                 if (b.h <= RR_MAX) {
 #pragma unroll 1
-                    for (int r = gt; r < b.h; r += LJ_NT) sm.A.rng[r] = row_range(D, uni.ko, b.y0 + r, false);
+                    for (int r = gt; r < b.h; r += LJ_NT) sm.A.rng[r] = row_range(D, kd, b.y0 + r, false);
                 } else if (e.n() <= PB_CAP) {
-                    const DiskF kf = uni.ko;
+                    const DiskF kf = kd;
 #pragma unroll 1
                     for (int i = gt; i < e.n(); i += LJ_NT)
                         sm.A.bm[i] = inside_f(D, kf, e.x0 + i % e.w, e.y0 + i / e.w, false) ? 1 : 0;
@@ -593,10 +660,10 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
         // from static solid and wall nodes within r_it comes per node from the
         // field precomputed with the geometry (the same table sum, taken once),
         // the force from surface nodes of nearby particles pair by pair.
-        if (forces && D.lj_psi != 0.0) {
+        {
             const int gt = threadIdx.x;
             const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
-            const Box b = uni.bo;
+            const Box b = bd;
             const Box e = {b.x0 - 1, b.y0 - 1, b.w + 2, b.h + 2};
             const bool use_bm = e.n() <= PB_CAP;
             const int ln = lj_n;
@@ -629,7 +696,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
                     if (x >= il && x <= ir) continue;
                     const int xx = x - b.x0;
                     sm.A.sxy[excl] = make_short2((short)xx, (short)gt);
-                    sm.A.arm[excl] = make_double2(min_image(x - q.x, D.nx, px), min_image(b.y0 + gt - q.y, D.ny, py));
+                    sm.A.arm[excl] = make_double2(min_image(x - cxd, D.nx, px), min_image(b.y0 + gt - cyd, D.ny, py));
                     ++excl;
                 }
                 __syncthreads();
@@ -655,7 +722,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
                             surf = !all_in;
                         }
                     } else {
-                        surf = is_surface(D, q.x, q.y, R, ax, ay);
+                        surf = is_surface(D, cxd, cyd, R, ax, ay);
                     }
                     if (surf) bits |= 1u << k;
                     if (++rx == b.w) { rx = 0; ++ry; }
@@ -670,8 +737,8 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
                         int yy = ry, xx = rx + k;
                         while (xx >= b.w) { xx -= b.w; ++yy; }
                         sm.A.sxy[excl] = make_short2((short)xx, (short)yy);
-                        sm.A.arm[excl] = make_double2(min_image(b.x0 + xx - q.x, D.nx, px),
-                                                      min_image(b.y0 + yy - q.y, D.ny, py));
+                        sm.A.arm[excl] = make_double2(min_image(b.x0 + xx - cxd, D.nx, px),
+                                                      min_image(b.y0 + yy - cyd, D.ny, py));
                         ++excl;
                     }
                 }
@@ -754,47 +821,23 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
         }
 #pragma unroll
         for (int c = 6; c < 9; ++c) {
-            const double x = (forces && D.lj_psi != 0.0) ? warp_sum(acc[c]) : 0.0;
+            const double x = warp_sum(acc[c]);
             if (lane == 0) sm.A.wsum[warp][c] = x;
         }
         __syncthreads();
-        if (forces && threadIdx.x < DIAG_N) {
-            // component groups: links 0-2 (warps 0-3), covered/uncovered 3-5 and
-            // 9-12 (warp 4), LJ 6-8 (all warps); fixed order
+        if (threadIdx.x >= 6 && threadIdx.x < 9) {
             const int c = threadIdx.x;
             double x = 0.0;
-            if (c < 3) x = ((sm.A.wsum[0][c] + sm.A.wsum[1][c]) + sm.A.wsum[2][c]) + sm.A.wsum[3][c];
-            else if (c < 6 || c >= 9) x = sm.A.wsum[4][c];
-            else
-                for (int w = 0; w < PBLOCK / 32; ++w) x += sm.A.wsum[w][c];
-            tot[c] = x;
-            a.diag[(int64_t)p * DIAG_N + c] = x;
-        }
-        __syncthreads();
-        if (advance && threadIdx.x == 0) {
-            // Eqs. MP5, MP6 (velocities) with r_c(t+1) = r_c(t) + U_p(t).
-            PartState n = q;
-            if (!st.fixed) {
-                if (forces) {
-                    const double Fx = (tot[0] + tot[3]) + tot[6], Fy = (tot[1] + tot[4]) + tot[7];
-                    const double T = (tot[2] + tot[5]) + tot[8];
-                    n.U = q.U + Fx * st.inv_m + st.buoy * D.gx;
-                    n.V = q.V + Fy * st.inv_m + st.buoy * D.gy;
-                    n.Om = q.Om + T * st.inv_I;
-                }
-                n.x = nxp;
-                n.y = nyp;
-                n.th = q.th + q.Om;
-                if (fabs(q.U) >= 1.0 || fabs(q.V) >= 1.0) atomicOr(a.err, ERR_STATE);  // faster than a node per step
-            }
-            a.state[(int64_t)(par ^ 1) * a.np + p] = n;
+            for (int w = 0; w < PBLOCK / 32; ++w) x += sm.A.wsum[w][c];
+            const int64_t tn = advance ? t + 1 : t;
+            a.ljf[4 * ((int64_t)(tn & 1) * a.np + p) + (c - 6)] = x;
         }
         return;
     }
 
     const int64_t t_next = advance ? t + 1 : t;
     const int wpar = (int)(t_next & 1);
-    if (role == 2) {
+    if (role == 3) {
         // ------------------------------------------------------------------ role C
         // Work items (row segments) within two nodes of the disk's boxes at t
         // and t+1 are "near": the stream-collide pass of that step runs them
@@ -1010,7 +1053,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
                 flips[idx] = (node << 1) | (int)((r >> 10) & 1u);
                 // the stream-collide pass of this step leaves this node's moments in flipmom[slot]
                 const int64_t slot = (int64_t)wpar * a.flips_total + idx;
-                a.fliptag[D.node_off + node] = stamp | (uint32_t)slot;
+                a.fliptag[(int64_t)((t + 1) & 1) * a.fliptag_stride + D.node_off + node] = stamp | (uint32_t)slot;
             }
             ++fex;
         }
@@ -1034,7 +1077,16 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes)
 
 cudaError_t launch_particle_step(int kind, const PartArgs& a, int modes, cudaStream_t s) {
     if (a.np <= 0) return cudaSuccess;
-    LBM_PDISPATCH(kind, (k_particle_step<S><<<3 * a.np, PBLOCK, 0, s>>>(a, modes)));
+    // the contiguous range of roles the modes ask for; roles inside the
+    // range that the modes leave out return at once
+    const bool on[4] = {(modes & (PL_FORCES | PL_SWAP)) != 0, (modes & PL_LJ) != 0, (modes & PL_RASTER) != 0,
+                        (modes & PL_MARK) != 0};
+    int r0 = 0, r1 = 3;
+    while (r0 < 4 && !on[r0]) ++r0;
+    while (r1 >= 0 && !on[r1]) --r1;
+    if (r0 > r1) return cudaSuccess;
+    const int grid = (r1 - r0 + 1) * a.np;
+    LBM_PDISPATCH(kind, (k_particle_step<S><<<grid, PBLOCK, 0, s>>>(a, modes, r0)));
     return cudaGetLastError();
 }
 

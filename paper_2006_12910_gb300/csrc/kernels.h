@@ -31,8 +31,10 @@ struct StreamArgs {
     const int32_t* near_cnt;  // [3]
     // Nodes that change side this step: a node whose tag carries step + 1
     // gets rho, sum f* e_x, sum f* e_y of its new populations written to
-    // flipmom[3 * slot] (only work items near particles are looked at).
+    // flipmom[3 * slot] (only work items near particles are looked at).  The
+    // tags of stamp s are in copy (s & 1), fliptag_stride nodes apart.
     const int64_t* fliptag;
+    int64_t fliptag_stride;
     double* flipmom;
 };
 enum { STREAM_ALL = 0, STREAM_FAR = 1, STREAM_NEAR = 2 };
@@ -96,10 +98,18 @@ struct PartArgs {
     int32_t* nflips;           // [2][np]
     int64_t links_total, flips_total;
     double* flipmom;           // [2][flips_total][3]: rho, sum f* e_x, sum f* e_y at the step of use
-    int64_t* fliptag;          // per node: (step << 32) | flip slot, for the stream-collide pass
+    int64_t* fliptag;          // [2][nodes]: (step << 32) | flip slot, copy (step & 1), for the stream-collide pass
+    int64_t fliptag_stride;
+    double* ljf;               // [2][np][4]: Eq. MP2 force x, y and torque on each particle at step s, copy (s & 1)
     double* diag;              // np * DIAG_N
     unsigned* err;
     const int64_t* ctr;        // step counter of the state in `arena`
+    // The force launch of step t from `arena` stores t + 1 here; the launches
+    // for later steps that follow it read it instead of a state counter that
+    // a concurrent stream-collide pass may already have advanced.  One word
+    // per arena: the next force launch from the same arena comes only after
+    // those launches have finished.
+    int64_t* pstep;
     int32_t* mark;             // [3][total_items]
     int32_t* near_list;        // [3][total_items]
     int32_t* near_cnt;         // [3]
@@ -109,9 +119,19 @@ struct PartArgs {
     const int32_t* lj_cnt;     // [ndom]
 };
 // Particle-step modes: forces + Newton-Euler, exchange of the link slots,
-// advance to t+1, rebuild of the link / flip lists, marking of the near items.
-enum { PL_FORCES = 1, PL_SWAP = 2, PL_ADVANCE = 4, PL_RASTER = 8, PL_MARK = 16 };
-constexpr int PL_STEP = PL_FORCES | PL_SWAP | PL_ADVANCE | PL_RASTER | PL_MARK;
+// advance to t+1, rebuild of the link / flip lists, marking of the near items,
+// the Eq. MP2 sum, and "ahead" (the step is one past the published counter).
+enum { PL_FORCES = 1, PL_SWAP = 2, PL_ADVANCE = 4, PL_RASTER = 8, PL_MARK = 16, PL_LJ = 32, PL_AHEAD = 64 };
+// Launches of step t: forces, exchange and Newton-Euler (role A); after it,
+// the rasterisation and marks for step t+1 (roles B, C) and the Eq. MP2 sum
+// for step t+2 (role D), each on its own stream.
+constexpr int PL_STEP_A = PL_FORCES | PL_SWAP | PL_ADVANCE;
+constexpr int PL_STEP_R = PL_RASTER | PL_MARK | PL_ADVANCE | PL_AHEAD;
+constexpr int PL_STEP_LJ = PL_LJ | PL_ADVANCE | PL_AHEAD;
+// set-up at the current step t: rasterisation and marks of t, then PL_SETUP_R
+// (rasterisation and marks of t+1), PL_LJ (Eq. MP2 at t) and
+// PL_LJ | PL_ADVANCE (Eq. MP2 at t+1)
+constexpr int PL_SETUP_R = PL_RASTER | PL_MARK | PL_ADVANCE;
 cudaError_t launch_particle_step(int kind, const PartArgs& a, int modes, cudaStream_t s);
 
 }  // namespace lbmk

@@ -159,7 +159,7 @@ template <class S>
 __device__ __noinline__ void flip_moments(const StreamArgs& a, const DomDev& D, int y, int x,
                                           const typename S::T* obase, int32_t stamp) {
     const int64_t ni = (int64_t)y * D.pitch + x;
-    const int64_t tag = a.fliptag[D.node_off + ni];
+    const int64_t tag = a.fliptag[(int64_t)(stamp & 1) * a.fliptag_stride + D.node_off + ni];
     if ((int32_t)(tag >> 32) != stamp) return;
     const uint32_t slot = (uint32_t)tag;
     double r = 0.0, jx = 0.0, jy = 0.0;
