@@ -32,6 +32,7 @@
 namespace lbmk {
 
 constexpr int PBLOCK = 256;
+constexpr int A_BLOCK = 160;  // role A launched alone: five warps
 
 __device__ __forceinline__ double min_image(double d, int L, bool periodic) {
     if (!periodic) return d;
@@ -354,7 +355,10 @@ union SmemU {
     SmemB B;
 };
 
-template <class S>
+// LO..HI: the roles an instantiation can run (the code of the others is left
+// out, so each launch fetches only its own instructions); role0 >= LO picks
+// the first role of the launch.
+template <class S, int LO, int HI>
 __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes, int role0) {
     typedef typename S::A A;
     // 0: forces, exchange and Newton-Euler; 1: Eq. MP2 for the next step;
@@ -369,6 +373,14 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
     const int64_t t = (modes & PL_AHEAD) ? *a.pstep : *a.ctr;
     const PartStatic st = a.st[p];
     const PartState q0 = a.state[p], q1 = a.state[(int64_t)a.np + p];
+    // role A: the list lengths of both parities in the same round trip
+    int nl2[2] = {0, 0}, nf2[2] = {0, 0};
+    if (LO == 0 && role == 0) {
+        nl2[0] = a.nlinks[p];
+        nl2[1] = a.nlinks[(int64_t)a.np + p];
+        nf2[0] = a.nflips[p];
+        nf2[1] = a.nflips[(int64_t)a.np + p];
+    }
     const bool advance = modes & PL_ADVANCE;
     // The near-item list of step t+2 is touched by nobody during this step.
     if (role == 0 && p == 0 && threadIdx.x == 0 && advance) {
@@ -394,29 +406,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
     __shared__ int sh_warp[PBLOCK / 32];
     __shared__ int near[MAXNEAR];
     __shared__ DiskF near_d[MAXNEAR];
-    // Per-particle quantities the whole CTA uses, computed once: FP64 issue
-    // is scarce on this part, so no warp repeats another's FP64 work.
-    struct Uni {
-        double nxp, nyp;
-        Box bo, bn;  // boxes of the disk at t and at t+1
-        DiskF ko, kn;
-    };
-    __shared__ Uni uni;
-    if (threadIdx.x == 0) {  // the disk at t
-        uni.bo = disk_box(q.x, q.y, R);
-        uni.ko = make_diskf(q.x, q.y, R);
-    } else if (threadIdx.x == 32) {  // the disk at t+1, in another warp so the two FP64 chains overlap
-        double x1 = q.x, y1 = q.y;
-        if (advance) next_position(D, q, st.fixed, x1, y1);
-        uni.nxp = x1;
-        uni.nyp = y1;
-        uni.bn = disk_box(x1, y1, R);
-        uni.kn = make_diskf(x1, y1, R);
-    }
-    __syncthreads();
-    const double nxp = uni.nxp, nyp = uni.nyp;
-
-    if (role == 0) {
+    if (LO == 0 && role == 0) {
         // ------------------------------------------------------------------ role A
         // Warps 0-3: the links, each with the force of Eq. MP1 and then the
         // exchange of Eqs. MP7-MP8 on the same two slots (they belong to this
@@ -425,10 +415,14 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
         // Each warp sums its own terms by shuffles in a fixed order and the
         // warps are added in a fixed order, so the totals are deterministic.
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        __shared__ double wsa[A_BLOCK / 32][DIAG_N];  // per-warp partial sums
         const int32_t* links = a.links + (int64_t)par * a.links_total;
         const int32_t* flips = a.flips + (int64_t)par * a.flips_total;
-        const int nl = a.nlinks[(int64_t)par * a.np + p];
-        const int nf = a.nflips[(int64_t)par * a.np + p];
+        const int nl = nl2[par], nf = nf2[par];
+        // the Eq. MP2 sums of t, loaded now by the threads that add them up
+        double ljc = 0.0;
+        if (threadIdx.x >= 6 && threadIdx.x < 9 && D.lj_psi != 0.0)
+            ljc = a.ljf[4 * ((int64_t)par * a.np + p) + (threadIdx.x - 6)];
         const bool forces = modes & PL_FORCES, swap = modes & PL_SWAP;
         double acc[DIAG_N];
 #pragma unroll
@@ -491,11 +485,11 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const double x = warp_sum(acc[c]);
-                    if (lane == 0) sm.A.wsum[warp][c] = x;
+                    if (lane == 0) wsa[warp][c] = x;
                 }
             } else if (lane == 0) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) sm.A.wsum[warp][c] = 0.0;
+                for (int c = 0; c < 3; ++c) wsa[warp][c] = 0.0;
             }
         } else if (warp == 4) {
             // Covered (+) / uncovered (-) nodes: F = +- rho (u - U_p), with rho and
@@ -525,7 +519,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
             for (int c = 3; c < DIAG_N; ++c) {
                 if (c >= 6 && c < 9) continue;
                 const double x = any ? warp_sum(acc[c]) : 0.0;
-                if (lane == 0) sm.A.wsum[4][c] = x;
+                if (lane == 0) wsa[4][c] = x;
             }
         }
         __syncthreads();
@@ -534,9 +528,9 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
             // 9-12 (warp 4), LJ 6-8 (role D, earlier launch); fixed order
             const int c = threadIdx.x;
             double x = 0.0;
-            if (c < 3) x = ((sm.A.wsum[0][c] + sm.A.wsum[1][c]) + sm.A.wsum[2][c]) + sm.A.wsum[3][c];
-            else if (c < 6 || c >= 9) x = sm.A.wsum[4][c];
-            else if (D.lj_psi != 0.0) x = a.ljf[4 * ((int64_t)par * a.np + p) + (c - 6)];
+            if (c < 3) x = ((wsa[0][c] + wsa[1][c]) + wsa[2][c]) + wsa[3][c];
+            else if (c < 6 || c >= 9) x = wsa[4][c];
+            else x = ljc;
             tot[c] = x;
             a.diag[(int64_t)p * DIAG_N + c] = x;
         }
@@ -552,8 +546,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
                     n.V = q.V + Fy * st.inv_m + st.buoy * D.gy;
                     n.Om = q.Om + T * st.inv_I;
                 }
-                n.x = nxp;
-                n.y = nyp;
+                next_position(D, q, false, n.x, n.y);
                 n.th = q.th + q.Om;
                 if (fabs(q.U) >= 1.0 || fabs(q.V) >= 1.0) atomicOr(a.err, ERR_STATE);  // faster than a node per step
             }
@@ -562,7 +555,30 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
         return;
     }
 
-    if (role == 1) {
+    if (HI < 1) return;
+    // Per-particle quantities the whole CTA uses, computed once: FP64 issue
+    // is scarce on this part, so no warp repeats another's FP64 work.
+    struct Uni {
+        double nxp, nyp;
+        Box bo, bn;  // boxes of the disk at t and at t+1
+        DiskF ko, kn;
+    };
+    __shared__ Uni uni;
+    if (threadIdx.x == 0) {  // the disk at t
+        uni.bo = disk_box(q.x, q.y, R);
+        uni.ko = make_diskf(q.x, q.y, R);
+    } else if (threadIdx.x == 32) {  // the disk at t+1, in another warp so the two FP64 chains overlap
+        double x1 = q.x, y1 = q.y;
+        if (advance) next_position(D, q, st.fixed, x1, y1);
+        uni.nxp = x1;
+        uni.nyp = y1;
+        uni.bn = disk_box(x1, y1, R);
+        uni.kn = make_diskf(x1, y1, R);
+    }
+    __syncthreads();
+    const double nxp = uni.nxp, nyp = uni.nyp;
+
+    if (LO <= 1 && role == 1) {
         // ------------------------------------------------------------------ role D
         // Eq. MP2 on p at the step this launch advances to (t+1, or t
         // without PL_ADVANCE): it needs only positions, and r_c(t+1) =
@@ -835,9 +851,10 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
         return;
     }
 
+    if (HI < 2) return;
     const int64_t t_next = advance ? t + 1 : t;
     const int wpar = (int)(t_next & 1);
-    if (role == 3) {
+    if (HI >= 3 && role == 3) {
         // ------------------------------------------------------------------ role C
         // Work items (row segments) within two nodes of the disk's boxes at t
         // and t+1 are "near": the stream-collide pass of that step runs them
@@ -1086,7 +1103,13 @@ cudaError_t launch_particle_step(int kind, const PartArgs& a, int modes, cudaStr
     while (r1 >= 0 && !on[r1]) --r1;
     if (r0 > r1) return cudaSuccess;
     const int grid = (r1 - r0 + 1) * a.np;
-    LBM_PDISPATCH(kind, (k_particle_step<S><<<grid, PBLOCK, 0, s>>>(a, modes, r0)));
+    // role A alone uses warps 0-4 only (links, covered / uncovered nodes): a
+    // smaller CTA finds room sooner beside a running stream-collide pass
+    const int block = r1 == 0 ? A_BLOCK : PBLOCK;
+    if (r1 == 0) LBM_PDISPATCH(kind, (k_particle_step<S, 0, 0><<<grid, block, 0, s>>>(a, modes, r0)))
+    else if (r0 == 1 && r1 == 1) LBM_PDISPATCH(kind, (k_particle_step<S, 1, 1><<<grid, block, 0, s>>>(a, modes, r0)))
+    else if (r0 >= 2) LBM_PDISPATCH(kind, (k_particle_step<S, 2, 3><<<grid, block, 0, s>>>(a, modes, r0)))
+    else return cudaErrorInvalidValue;  // role A or D together with other roles: no such launch
     return cudaGetLastError();
 }
 
