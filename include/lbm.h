@@ -202,6 +202,15 @@ int lbm_get_launch(const lbm_ctx* ctx, int64_t* out4);
  * exactly as with lbm_step. */
 int lbm_profile_steps(lbm_ctx* ctx, int64_t nsteps, double* ms_out3, int64_t* launches_out);
 
+/* Measurement of the stream-and-collide kernel alone: nlaunches passes over
+ * every work item, back to back on the context stream, each from the current
+ * state into the other population arena, with one CUDA-event pair around
+ * them; *ms_out receives their total device time.  The state does not
+ * advance (the next step rewrites what the passes wrote: the same values),
+ * so the number is the kernel's sustained time per launch in a busy stream.
+ * Blocking.  LBM_E_INVAL for nlaunches < 1 or ms_out NULL. */
+int lbm_time_stream(lbm_ctx* ctx, int32_t nlaunches, double* ms_out);
+
 /* Largest row count lbm_checks_noalloc accepts (its static scratch holds one
  * FP64 triple per row). */
 #define LBM_NOALLOC_MAX_ROWS 16384

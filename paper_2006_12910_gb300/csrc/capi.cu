@@ -1248,6 +1248,28 @@ int lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double* ms_out3, int64_t* laun
     return check_err(c);
 }
 
+int lbm_time_stream(lbm_ctx* c, int32_t nlaunches, double* ms_out) {
+    if (!c) return LBM_E_INVAL;
+    if (nlaunches < 1 || !ms_out) return fail(c, LBM_E_INVAL, "nlaunches must be >= 1 and ms_out not NULL");
+    int r = sync_and_check(c);
+    if (r) return r;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CKC(c, cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+    for (int k = 0; k < nlaunches && e == cudaSuccess; ++k)
+        e = enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    CKC(c, e);
+    *ms_out = ms;
+    return check_err(c);
+}
+
 int lbm_autotune(lbm_ctx* c, int trial_steps) {
     if (!c) return LBM_E_INVAL;
     if (trial_steps < 1) trial_steps = 20;

@@ -25,7 +25,7 @@ EXPORTED = [
     "lbm_create", "lbm_create_ensemble", "lbm_set_geometry", "lbm_add_particles", "lbm_set_populations",
     "lbm_get_populations", "lbm_step", "lbm_sync", "lbm_moments", "lbm_moments_device", "lbm_moments_async",
     "lbm_moments_async_wait", "lbm_particles", "lbm_particle_forces", "lbm_checks", "lbm_step_count",
-    "lbm_save", "lbm_load", "lbm_autotune", "lbm_set_launch", "lbm_get_launch", "lbm_profile_steps",
+    "lbm_save", "lbm_load", "lbm_autotune", "lbm_set_launch", "lbm_get_launch", "lbm_profile_steps", "lbm_time_stream",
     "lbm_checks_noalloc", "lbm_last_error", "lbm_destroy",
 ]
 NOALLOC_MAX_ROWS = 16384
@@ -107,6 +107,7 @@ def load(build_if_missing: bool = True):
             "lbm_set_launch": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
             "lbm_get_launch": (ctypes.c_int, [_vp, _P(ctypes.c_int64)]),
             "lbm_profile_steps": (ctypes.c_int, [_vp, ctypes.c_int64, _dp, _P(ctypes.c_int64)]),
+            "lbm_time_stream": (ctypes.c_int, [_vp, ctypes.c_int32, _dp]),
             "lbm_checks_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                   ctypes.c_int32, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp]),
             "lbm_last_error": (ctypes.c_char_p, [_vp]),
@@ -272,11 +273,17 @@ class Context:
         self._ck(self.L.lbm_load(self.h, str(path).encode()))
 
     def profile_steps(self, n):
-        """Run n steps with per-kernel CUDA events: (ms forces, ms links, ms stream-collide, launches)."""
+        """Run n steps with per-kernel CUDA events: (ms force launch, ms raster + LJ launches, ms stream-collide, launches)."""
         out = np.zeros(3)
         nl = ctypes.c_int64(0)
         self._ck(self.L.lbm_profile_steps(self.h, int(n), out.ctypes.data_as(_dp), ctypes.byref(nl)))
         return float(out[0]), float(out[1]), float(out[2]), int(nl.value)
+
+    def time_stream(self, n):
+        """Total device ms of n back-to-back stream-collide passes over every item (state not advanced)."""
+        ms = ctypes.c_double(0.0)
+        self._ck(self.L.lbm_time_stream(self.h, int(n), ctypes.byref(ms)))
+        return float(ms.value)
 
     def autotune(self, trial_steps=20):
         self._ck(self.L.lbm_autotune(self.h, int(trial_steps)))
