@@ -180,10 +180,12 @@ int lbm_autotune(lbm_ctx* ctx, int trial_steps);
 /* Launch configuration of the stream-and-collide kernel (no paper
  * counterpart; it selects among equivalent implementations of Eqs. e.LB1 /
  * e.LB2, all with the same results).  kernel: 0 register-pipelined with one
- * warp item per warp, 1 the same with a persistent grid-stride grid, 2 staged
- * through shared memory with bulk asynchronous copies (`stages` row segments
- * in flight per warp, 1..8; block at most 256 threads).  block: threads per
- * CTA, a multiple of 32, at most 128 for kernels 0 and 1.  LBM_E_INVAL for values out of range
+ * warp item per warp, 1 the same with a grid-stride grid of 16 CTAs' worth of
+ * warps per SM, 2 staged through shared memory with bulk asynchronous copies
+ * (`stages` row segments in flight per warp, 1..8; block at most 256
+ * threads), 3 register kernel on a grid-stride grid of only the CTAs that fit
+ * the SMs at once.  block: threads per CTA, a multiple of 32, at most
+ * 128 for kernels 0, 1 and 3.  LBM_E_INVAL for values out of range
  * or a staged configuration whose shared memory does not fit an SM; the
  * previous configuration then stays.  lbm_get_launch writes {kernel, block,
  * stages, grid} to out4. */
@@ -203,9 +205,10 @@ int lbm_get_launch(const lbm_ctx* ctx, int64_t* out4);
 int lbm_profile_steps(lbm_ctx* ctx, int64_t nsteps, double* ms_out3, int64_t* launches_out);
 
 /* Measurement of the stream-and-collide kernel alone: nlaunches passes over
- * every work item, back to back on the context stream, each from the current
- * state into the other population arena, with one CUDA-event pair around
- * them; *ms_out receives their total device time.  The state does not
+ * every work item (the variant without the moments of nodes that change side
+ * under a particle), back to back on the context stream, each from the
+ * current state into the other population arena, with one CUDA-event pair
+ * around them; *ms_out receives their total device time.  The state does not
  * advance (the next step rewrites what the passes wrote: the same values),
  * so the number is the kernel's sustained time per launch in a busy stream.
  * Blocking.  LBM_E_INVAL for nlaunches < 1 or ms_out NULL. */

@@ -96,7 +96,9 @@ struct lbm_ctx {
     int cur = 0;
     int64_t steps = 0;
     int block = 128;
-    int grid_mode = 1;  // 0: one warp item per warp; 1: persistent grid-stride; 2: staged kernel
+    // 0: one warp item per warp; 1: grid-stride over 16 CTAs per SM; 2: staged
+    // kernel; 3: grid-stride over the CTAs that fit the SMs at once
+    int grid_mode = 1;
     int stages = 0;     // row segments in flight per warp of the staged kernel
     int64_t grid = 1;
 
@@ -289,12 +291,14 @@ void set_launch(lbm_ctx* c) {
         const int64_t share = (c->total_items + max_warps - 1) / max_warps;
         const int64_t warps = (c->total_items + share - 1) / std::max<int64_t>(share, 1);
         c->grid = std::max<int64_t>(1, (warps + wpb - 1) / wpb);
-    } else if (c->grid_mode == 1) {
+    } else if (c->grid_mode == 1 || c->grid_mode == 3) {
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int64_t per_sm = std::max<int64_t>(1, 2048 / c->block);
-        c->grid = std::min<int64_t>(full, (int64_t)sms * per_sm);
+        const int64_t resident =
+            (int64_t)sms * std::max(1, reg_blocks_per_sm(c->kind, c->noise, c->pl, c->block));
+        c->grid = std::min<int64_t>(full, c->grid_mode == 1 ? (int64_t)sms * per_sm : resident);
     } else {
         c->grid = full;
     }
@@ -342,8 +346,10 @@ PartArgs part_args(lbm_ctx* c, int cur) {
     return a;
 }
 
+// with_flips = false leaves out the moments of nodes changing side (a pass
+// that only times the kernel does not need them).
 cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int block, int64_t grid,
-                                   int mode = STREAM_ALL) {
+                                   int mode = STREAM_ALL, bool with_flips = true) {
     StreamArgs a;
     a.doms = c->dd;
     a.item_off = c->d_item_off;
@@ -358,7 +364,7 @@ cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int bloc
     a.ctr_out = c->ctr + (cur ^ 1);
     a.err = c->err;
     a.mode = mode;
-    a.flips = c->np_active > 0 && mode != STREAM_FAR;
+    a.flips = with_flips && c->np_active > 0 && mode != STREAM_FAR;
     a.mark = c->mark;
     a.near_list = c->near_list;
     a.near_cnt = c->near_cnt;
@@ -1258,7 +1264,7 @@ int lbm_time_stream(lbm_ctx* c, int32_t nlaunches, double* ms_out) {
     cudaError_t e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
     for (int k = 0; k < nlaunches && e == cudaSuccess; ++k)
-        e = enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid);
+        e = enqueue_stream_collide(c, c->cur, c->stream, c->block, c->grid, STREAM_ALL, false);
     if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -1282,7 +1288,11 @@ int lbm_autotune(lbm_ctx* c, int trial_steps) {
     // the register kernel at 128 threads; fewer threads per CTA time faster
     // alone but lose in the overlapped step (more CTAs to place beside the
     // particle kernel)
-    for (int mode = 0; mode < 2; ++mode) cands.push_back({mode, 128, 0});
+    // a grid of resident CTAs only (3) holds every SM for the whole pass: in a
+    // step with particles the particle launches then wait for the pass to end
+    // (measured slower there), so it is tried only without particles
+    for (int mode : {0, 1, 3})
+        if (c->np_active == 0 || mode < 2) cands.push_back({mode, 128, 0});
     for (Cand k : {Cand{2, 32, 1}, Cand{2, 64, 1}, Cand{2, 64, 2}, Cand{2, 128, 1}, Cand{2, 128, 2}, Cand{2, 256, 1}})
         if (staged_blocks_per_sm(c->kind, c->noise, c->pl, k.block, k.stages) > 0) cands.push_back(k);
     cudaEvent_t e0, e1;
@@ -1317,9 +1327,9 @@ int lbm_autotune(lbm_ctx* c, int trial_steps) {
 
 int lbm_set_launch(lbm_ctx* c, int32_t kernel, int32_t block, int32_t stages) {
     if (!c) return LBM_E_INVAL;
-    if (kernel < 0 || kernel > 2 || block < 32 || block > 512 || block % 32 != 0)
-        return fail(c, LBM_E_INVAL, "kernel must be 0..2 and block a multiple of 32 in [32, 512]");
-    if (kernel < 2 && block > REG_K1_MAX_BLOCK)
+    if (kernel < 0 || kernel > 3 || block < 32 || block > 512 || block % 32 != 0)
+        return fail(c, LBM_E_INVAL, "kernel must be 0..3 and block a multiple of 32 in [32, 512]");
+    if (kernel != 2 && block > REG_K1_MAX_BLOCK)
         return fail(c, LBM_E_INVAL, "the register kernel runs at most 128 threads per CTA");
     if (kernel == 2) {
         if (stages < 1 || stages > STAGED_MAX_STAGES || block > STAGED_MAX_BLOCK)

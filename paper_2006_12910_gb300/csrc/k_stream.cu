@@ -5,9 +5,9 @@
 // Layout: structure of arrays, plane i of domain d at arena[off + i*plane],
 // rows of `pitch` elements, x fastest.  The stored values are the
 // post-collision populations f*(t).  Each lane owns V consecutive nodes of
-// one row (V*sizeof(T) = 16 bytes), a warp owns 32 such chunks; a work item
-// is one (domain, row, warp segment).  For every direction the lane loads the
-// 16-byte vector of the source row and, for the two x-shifted families, one
+// one row (V*sizeof(T) = 8 or 16 bytes), a warp owns 32 such chunks; a work
+// item is one (domain, row, warp segment).  For every direction the lane loads
+// the vector of the source row and, for the two x-shifted families, one
 // extra element at the chunk edge (served by L1 from the neighbour lane's
 // sector), then collides in registers and writes 16-byte vectors.
 //
@@ -24,13 +24,12 @@
 
 namespace lbmk {
 
-// At most 128 threads per CTA.  The plain FP32 variants also ask for five
-// CTAs per SM: the compiler then keeps them at 96 registers (20 resident warps
-// per SM) without spilling, measured faster than 124-128 registers; noise and
-// power-law FP32 variants keep 128, FP64 and half-precision ones (twice the
-// values per lane or per node) up to 168.
+// At most 128 threads per CTA, and the storage kind's resident CTAs per SM
+// (MINB / MINB_EXT): the register cap they imply keeps the common variants
+// from spilling while leaving room for as many warps as possible (plain FP32
+// and half-precision kinds: 96 registers, 20 warps per SM).
 template <class S, bool NOISE, bool PL>
-constexpr int k1_min_blocks() { return S::V == 4 ? ((!NOISE && !PL) ? 5 : 4) : 3; }
+constexpr int k1_min_blocks() { return (!NOISE && !PL) ? S::MINB : S::MINB_EXT; }
 
 template <class S, bool NOISE, bool PL, bool FLIPS>
 __global__ void __launch_bounds__(REG_K1_MAX_BLOCK, (k1_min_blocks<S, NOISE, PL>())) k_stream_collide(StreamArgs a) {
@@ -152,6 +151,29 @@ cudaError_t launch_stream_collide(int kind, bool noise, bool pl, const StreamArg
         case 3: return launch_kind<StF16S>(noise, pl, a, block, grid, s);
         case 4: return launch_kind<StBF16S>(noise, pl, a, block, grid, s);
         default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class S>
+static int reg_bps(bool noise, bool pl, int block) {
+    int n = 0;
+    cudaError_t e;
+    if (noise && pl) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream_collide<S, true, true, false>, block, 0);
+    else if (noise) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream_collide<S, true, false, false>, block, 0);
+    else if (pl) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream_collide<S, false, true, false>, block, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream_collide<S, false, false, false>, block, 0);
+    return e == cudaSuccess ? n : 0;
+}
+
+int reg_blocks_per_sm(int kind, bool noise, bool pl, int block) {
+    if (block < 32 || block > REG_K1_MAX_BLOCK) return 0;
+    switch (kind) {
+        case 0: return reg_bps<StF64>(noise, pl, block);
+        case 1: return reg_bps<StF32>(noise, pl, block);
+        case 2: return reg_bps<StF32S>(noise, pl, block);
+        case 3: return reg_bps<StF16S>(noise, pl, block);
+        case 4: return reg_bps<StBF16S>(noise, pl, block);
+        default: return 0;
     }
 }
 

@@ -46,6 +46,9 @@ enum { STREAM_ALL = 0, STREAM_FAR = 1, STREAM_NEAR = 2 };
 cudaError_t launch_stream_collide(int kind, bool noise, bool pl, const StreamArgs& a, int block, int64_t grid,
                                   int stages, cudaStream_t s);
 int store_vector_width(int kind);
+// CTAs of the register kernel (no flip moments) that fit on one SM at `block`
+// threads, for the storage kind and collision variant (0 on error).
+int reg_blocks_per_sm(int kind, bool noise, bool pl, int block);
 // Dynamic shared memory of one CTA of the staged kernel, and how many such
 // CTAs fit on one SM (0 when none does or the arguments are out of range).
 size_t staged_smem_bytes(int kind, int block, int stages);

@@ -40,32 +40,44 @@ __host__ __device__ constexpr double inv_sqrt_wk(int k) {
 __host__ __device__ constexpr double noise_coef(int i, int k) { return wgt(i) * mode_vec(k, i) * inv_sqrt_wk(k); }
 
 // ---------------------------------------------------------------------------
-// Population storage kinds.  V = nodes per 16-byte vector.
+// Population storage kinds.  V = consecutive nodes of one row a lane owns in
+// the register stream-collide kernel (one vector load or store of V*sizeof(T)
+// = 8 or 16 bytes per plane).  MINB / MINB_EXT: CTAs of 128 threads the
+// register kernel asks to keep resident per SM (plain BGK / with noise or
+// the power law), which caps its registers per thread.
 // ---------------------------------------------------------------------------
 struct StF64 {
     typedef double T; typedef double A;
     static constexpr int V = 2; static constexpr bool SHIFT = false; static constexpr bool SCALED = false;
     static constexpr int KIND = 0;
+    static constexpr int MINB = 3, MINB_EXT = 3;
 };
 struct StF32 {
     typedef float T; typedef float A;
     static constexpr int V = 4; static constexpr bool SHIFT = false; static constexpr bool SCALED = false;
     static constexpr int KIND = 1;
+    static constexpr int MINB = 5, MINB_EXT = 4;
 };
 struct StF32S {
     typedef float T; typedef float A;
     static constexpr int V = 4; static constexpr bool SHIFT = true; static constexpr bool SCALED = false;
     static constexpr int KIND = 2;
+    static constexpr int MINB = 5, MINB_EXT = 4;
 };
+// Half-precision kinds take 8-byte vectors (4 nodes per lane): the register
+// footprint of an FP32 lane, so five CTAs fit per SM, and chunks near solids
+// store 4 rather than 8 nodes one by one.
 struct StF16S {
     typedef __half T; typedef float A;
-    static constexpr int V = 8; static constexpr bool SHIFT = true; static constexpr bool SCALED = true;
+    static constexpr int V = 4; static constexpr bool SHIFT = true; static constexpr bool SCALED = true;
     static constexpr int KIND = 3;
+    static constexpr int MINB = 5, MINB_EXT = 4;
 };
 struct StBF16S {
     typedef __nv_bfloat16 T; typedef float A;
-    static constexpr int V = 8; static constexpr bool SHIFT = true; static constexpr bool SCALED = true;
+    static constexpr int V = 4; static constexpr bool SHIFT = true; static constexpr bool SCALED = true;
     static constexpr int KIND = 4;
+    static constexpr int MINB = 5, MINB_EXT = 4;
 };
 
 __device__ __forceinline__ double to_a(double v, double) { return v; }
@@ -77,20 +89,26 @@ __device__ __forceinline__ void from_a(float v, float, float& o) { o = v; }
 __device__ __forceinline__ void from_a(float v, float s, __half& o) { o = __float2half_rn(v * s); }
 __device__ __forceinline__ void from_a(float v, float s, __nv_bfloat16& o) { o = __float2bfloat16_rn(v * s); }
 
-// 16-byte vector load (read-only path) and store of V consecutive elements.
+// Vector load (read-only path) and store of V consecutive elements: one
+// 8- or 16-byte access.
+template <int B> struct VecOf;
+template <> struct VecOf<8> { typedef uint2 type; };
+template <> struct VecOf<16> { typedef uint4 type; };
 template <class S>
 __device__ __forceinline__ void load_vec(const typename S::T* p, typename S::A* out, typename S::A inv) {
-    union { uint4 u; typename S::T t[S::V]; } r;
-    r.u = __ldg(reinterpret_cast<const uint4*>(p));
+    typedef typename VecOf<S::V * sizeof(typename S::T)>::type VT;
+    union { VT u; typename S::T t[S::V]; } r;
+    r.u = __ldg(reinterpret_cast<const VT*>(p));
 #pragma unroll
     for (int k = 0; k < S::V; ++k) out[k] = to_a(r.t[k], inv);
 }
 template <class S>
 __device__ __forceinline__ void store_vec(typename S::T* p, const typename S::A* in, typename S::A scale) {
-    union { uint4 u; typename S::T t[S::V]; } r;
+    typedef typename VecOf<S::V * sizeof(typename S::T)>::type VT;
+    union { VT u; typename S::T t[S::V]; } r;
 #pragma unroll
     for (int k = 0; k < S::V; ++k) from_a(in[k], scale, r.t[k]);
-    *reinterpret_cast<uint4*>(p) = r.u;
+    *reinterpret_cast<VT*>(p) = r.u;
 }
 template <class S>
 __device__ __forceinline__ typename S::A load_one(const typename S::T* p, typename S::A inv) {

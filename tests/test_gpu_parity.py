@@ -283,8 +283,10 @@ def test_invalid_calls_raise():
 
 def test_full_size_porous_workload(errlog):
     """The benchmark workload at full size (2048x1024, ~300 obstacles, 20 particles,
-    Zou-He ends, FP32 shifted store, the bench's launch shape), 10 steps, every node
-    compared with the oracle."""
+    Zou-He ends, FP32 shifted store), 10 steps, every node compared with the
+    oracle, on each launch shape the benchmark's autotuner may pick for the
+    register kernel (one item per warp, grid-stride, resident-only grid); the
+    three must agree bit for bit."""
     w = workloads.porous()
     base = dict(nx=w.nx, ny=w.ny, **w.params)
     f0 = np.empty((9, w.ny, w.nx))
@@ -292,10 +294,21 @@ def test_full_size_porous_workload(errlog):
     ref, ctx = pair(base, "f32s", solid=w.solid, particles=w.particles, f0=f0)
     oracle.set_threads(0)
     ref.step(10)
-    ctx.step(10)
-    errs, _ = compare_state(ref, ctx, "f32s", w.solid)
-    pr, pg = ref.particles(), ctx.particles()
-    perr = max(abs(a[k] - b[k]) for a, b in zip(pr, pg) for k in ("x", "y", "U", "V"))
-    errlog(**errs, particle=perr)
-    assert errs["rho"] < 1e-6 and errs["f"] < 1e-6 and errs["u"] < 1e-3
-    assert perr < 1e-6
+    first = None
+    for launch in [(1, 128, 0), (0, 128, 0), (3, 128, 0)]:
+        if first is not None:
+            _, ctx = pair(base, "f32s", solid=w.solid, particles=w.particles, f0=f0)
+        ctx.set_launch(*launch)
+        ctx.step(10)
+        errs, _ = compare_state(ref, ctx, "f32s", w.solid)
+        pr, pg = ref.particles(), ctx.particles()
+        perr = max(abs(a[k] - b[k]) for a, b in zip(pr, pg) for k in ("x", "y", "U", "V"))
+        errlog(launch=launch, **errs, particle=perr)
+        assert errs["rho"] < 1e-6 and errs["f"] < 1e-6 and errs["u"] < 1e-3
+        assert perr < 1e-6
+        f = ctx.populations()
+        if first is None:
+            first = f
+        else:
+            assert np.array_equal(f, first), launch
+        ctx.close()

@@ -1,6 +1,8 @@
 """The staged stream-collide kernel (row segments brought into shared memory by
-bulk asynchronous copies, kernel 2 of lbm_set_launch) against the FP64 oracle,
-and bitwise against the register-pipelined kernel.
+bulk asynchronous copies, kernel 2 of lbm_set_launch) and the register kernel
+on a resident-only grid (kernel 3, several items per warp) against the FP64
+oracle, and bitwise against the register-pipelined kernel with one item per
+warp.
 
 Both kernels run the same per-node arithmetic in the same order, so on the same
 inputs their stored populations must be identical bit for bit; the oracle
@@ -20,7 +22,8 @@ from oracle import oracle
 from paper_2006_12910_gb300 import lbm, workloads
 
 pytestmark = pytest.mark.gpu
-STAGED = [(2, 64, 4), (2, 128, 2), (2, 128, 3), (2, 256, 1)]
+# staged configurations, and the register kernel on a grid of resident CTAs only (3)
+STAGED = [(2, 64, 4), (2, 128, 2), (2, 128, 3), (2, 256, 1), (3, 128, 0), (3, 32, 0)]
 STORES = ["f64", "f32", "f32s", "f16s", "bf16s"]
 
 
@@ -105,7 +108,7 @@ def test_staged_power_law(store, errlog):
     errlog(store=store, **errs)
 
 
-@pytest.mark.parametrize("launch", [(2, 128, 3), (2, 64, 4)])
+@pytest.mark.parametrize("launch", [(2, 128, 3), (2, 64, 4), (3, 128, 0)])
 @pytest.mark.parametrize("store", ["f64", "f32s", "f16s"])
 def test_staged_particles_overlapped(store, launch, errlog):
     """Particles: the items away from particles run on the staged kernel, the
@@ -136,7 +139,7 @@ def test_staged_ensemble(store, errlog):
         plist.append(w.particles)
         f0s.append(f0)
     ctxs = []
-    for launch in [(0, 128, 0), (2, 128, 2)]:
+    for launch in [(0, 128, 0), (2, 128, 2), (3, 64, 0)]:
         ctx = lbm.Context(ps, particles=plist)
         for d, f0 in enumerate(f0s):
             ctx.set_populations(f0, dom=d)
@@ -148,6 +151,7 @@ def test_staged_ensemble(store, errlog):
     for d, r in enumerate(refs):
         a, b = ctxs[0].populations(dom=d), ctxs[1].populations(dom=d)
         assert np.array_equal(a, b), d
+        assert np.array_equal(a, ctxs[2].populations(dom=d)), d
         e = float(np.linalg.norm(b - r.populations()) / np.linalg.norm(r.populations()))
         errlog(store=store, dom=d, f=e)
         assert e < (1e-12 if store == "f64" else 1e-5)
@@ -163,7 +167,7 @@ def test_staged_many_items_per_warp():
     rng = np.random.default_rng(5)
     f0 = (oracle.feq(1.0, 0.0, 0.0)[:, None, None] * (1 + 0.01 * rng.standard_normal((9, ny, nx)))).astype(np.float64)
     ctxs = []
-    for launch in [(1, 128, 0), (2, 64, 2)]:
+    for launch in [(1, 128, 0), (2, 64, 2), (3, 128, 0)]:
         ctx = lbm.Context(gpu_params(base, "f32s", len(parts)), particles=[parts])
         ctx.set_populations(f0)
         ctx.set_launch(*launch)
@@ -174,17 +178,22 @@ def test_staged_many_items_per_warp():
     assert items > 32 * grid * (block // 32)
     assert np.array_equal(ctxs[0].populations(), ctxs[1].populations())
     assert ctxs[0].particles() == ctxs[1].particles()
+    k, block, stages, grid = ctxs[2].launch()
+    assert items > 8 * grid * (block // 32)  # several items per warp
+    assert np.array_equal(ctxs[0].populations(), ctxs[2].populations())
+    assert ctxs[0].particles() == ctxs[2].particles()
 
 
 def test_set_launch_rejects_bad_values():
     base = dict(nx=32, ny=32, periodic_x=1, periodic_y=1, walls_y=0, tau=0.8)
     ctx = lbm.Context(gpu_params(base, "f32s"))
     before = ctx.launch()
-    for bad in [(3, 128, 0), (0, 48, 0), (0, 1024, 0), (1, 256, 0), (2, 128, 0), (2, 128, 9), (2, 512, 2), (-1, 128, 0)]:
+    for bad in [(4, 128, 0), (0, 48, 0), (0, 1024, 0), (1, 256, 0), (3, 256, 0), (3, 160, 0), (2, 128, 0), (2, 128, 9),
+                (2, 512, 2), (-1, 128, 0)]:
         with pytest.raises(lbm.LbmError):
             ctx.set_launch(*bad)
         assert ctx.launch() == before
     ctx.set_launch(2, 128, 2)
     assert ctx.launch()[:3] == (2, 128, 2)
     ctx.autotune(3)
-    assert ctx.launch()[0] in (0, 1, 2)
+    assert ctx.launch()[0] in (0, 1, 2, 3)
