@@ -33,6 +33,12 @@ if ROOT not in sys.path:
 NCU_TRAFFIC = {("k_stream_collide", "f32s", 2048, 1024): 104.3e6}
 
 METRIC = "D2Q9 MLUPS and % HBM roofline, FP32/FP16-store vs FP64 path at stated error"
+# FP64 operations of one BGK collision with the velocity-shift force (unshifted FP64
+# store, no noise, no power law), an FMA counted as 2: 14 adds for the moments, 3 + 3
+# for the two shifted velocity components, 4 for 3/2 u.u, 1 for 3 rho, 6 for the rest
+# population, 4 x 16 for the four opposite pairs and 2 for the diagonal projections;
+# plus one division (1/rho), not counted.
+FP64_FLOPS_PER_NODE = 97
 UNIT = "MLUPS"
 STORE_BYTES = {"f64": 8, "f32": 4, "f32s": 4, "f16s": 2, "bf16s": 2}
 
@@ -413,6 +419,17 @@ def main():
             variants[store] = {"MLUPS": nodes * n3 / (m3 * 1e-3) / 1e6, "kernel_ms": k3,
                                "kernel_GBs": b3 / (k3 * 1e-3) / 1e9,
                                "frac": b3 / (k3 * 1e-3) / 1e9 / peak}
+            if store == "f64":
+                # FP64 arithmetic roofline: the collision's FP64 flops per fluid node (an FMA
+                # counts 2; the one division per node not counted) against the device's FP64
+                # FMA rate measured now by the library's probe.
+                fp64_peak = lbm.fp64_fma_rate(stream.cuda_stream)
+                achieved_gf = fluid * FP64_FLOPS_PER_NODE / (k3 * 1e-3) / 1e9
+                variants[store]["alu"] = {"bound": "fp64", "flops_per_node": FP64_FLOPS_PER_NODE,
+                                          "achieved_gflops": achieved_gf, "peak_gflops": fp64_peak,
+                                          "frac": achieved_gf / fp64_peak,
+                                          "hbm_floor_ms": b3 / (peak * 1e9) * 1e3,
+                                          "alu_floor_ms": fluid * FP64_FLOPS_PER_NODE / (fp64_peak * 1e9) * 1e3}
             c3.close()
 
     ens = None

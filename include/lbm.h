@@ -214,6 +214,16 @@ int lbm_profile_steps(lbm_ctx* ctx, int64_t nsteps, double* ms_out3, int64_t* la
  * Blocking.  LBM_E_INVAL for nlaunches < 1 or ms_out NULL. */
 int lbm_time_stream(lbm_ctx* ctx, int32_t nlaunches, double* ms_out);
 
+/* Measurement of the device's FP64 rate (no paper counterpart; it sets the
+ * arithmetic roofline of the FP64 store, whose collision is bound by FP64
+ * issue on this part rather than by HBM).  Eight independent FMA chains in
+ * every thread of 8 CTAs x 256 threads per SM, timed with CUDA events on
+ * cuda_stream (NULL: the default stream), best of three launches after one
+ * warm-up; *gflops_out = 2 x FMAs / second / 1e9.  Blocking; allocates
+ * nothing.  LBM_E_INVAL for gflops_out NULL, LBM_E_CUDA on a CUDA error
+ * (lbm_last_error(NULL) gives the reason). */
+int lbm_fp64_fma_rate(void* cuda_stream, double* gflops_out);
+
 /* Largest row count lbm_checks_noalloc accepts (its static scratch holds one
  * FP64 triple per row). */
 #define LBM_NOALLOC_MAX_ROWS 16384

@@ -1254,6 +1254,35 @@ int lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double* ms_out3, int64_t* laun
     return check_err(c);
 }
 
+int lbm_fp64_fma_rate(void* cuda_stream, double* gflops_out) {
+    if (!gflops_out) return fail(nullptr, LBM_E_INVAL, "gflops_out is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0, sms = 0;
+    CKC(nullptr, cudaGetDevice(&dev));
+    CKC(nullptr, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = 8 * sms, iters = 4096;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CKC(nullptr, cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = launch_fp64_fma(blocks, iters, s);  // warm-up
+    float best = 0.f;
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = launch_fp64_fma(blocks, iters, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (best == 0.f || ms < best)) best = ms;
+    }
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    CKC(nullptr, e);
+    const double fmas = (double)blocks * 256.0 * 8.0 * iters;
+    *gflops_out = 2.0 * fmas / (best * 1e-3) / 1e9;
+    return LBM_OK;
+}
+
 int lbm_time_stream(lbm_ctx* c, int32_t nlaunches, double* ms_out) {
     if (!c) return LBM_E_INVAL;
     if (nlaunches < 1 || !ms_out) return fail(c, LBM_E_INVAL, "nlaunches must be >= 1 and ms_out not NULL");

@@ -261,4 +261,30 @@ cudaError_t launch_checks(int kind, const DomDev& D, const void* arena, const ui
     return cudaGetLastError();
 }
 
+// FP64 fused multiply-add rate of the device (measurement only): every
+// thread runs eight independent FMA chains, so the FP64 pipe, not the latency
+// of one chain, sets the time.  The result feeds a sink that no real input
+// reaches, which keeps the chains alive without any output buffer.
+static __device__ double g_fma_sink;
+
+__global__ void __launch_bounds__(256) k_fp64_fma(int iters, double m, double c) {
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 1.0 + 1e-9 * (double)(threadIdx.x + 256 * k);
+#pragma unroll 1
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == -1.0) g_fma_sink = s;
+}
+
+cudaError_t launch_fp64_fma(int blocks, int iters, cudaStream_t s) {
+    k_fp64_fma<<<blocks, 256, 0, s>>>(iters, 0.999999999, 1e-12);
+    return cudaGetLastError();
+}
+
 }  // namespace lbmk

@@ -82,6 +82,8 @@ cudaError_t launch_moments(int kind, const DomDev& D, const void* arena, const u
 cudaError_t launch_checks(int kind, const DomDev& D, const void* arena, const uint8_t* solid, double* partial,
                           int nblocks, double* out, cudaStream_t s);
 constexpr int CHECK_BLOCKS = 304;
+// `blocks` CTAs of 256 threads, each thread 8 x iters FP64 FMAs (the FP64 rate probe).
+cudaError_t launch_fp64_fma(int blocks, int iters, cudaStream_t s);
 
 // ---- particle kernel (k_part.cu) ----
 struct PartArgs {

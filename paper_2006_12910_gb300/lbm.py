@@ -25,7 +25,7 @@ EXPORTED = [
     "lbm_create", "lbm_create_ensemble", "lbm_set_geometry", "lbm_add_particles", "lbm_set_populations",
     "lbm_get_populations", "lbm_step", "lbm_sync", "lbm_moments", "lbm_moments_device", "lbm_moments_async",
     "lbm_moments_async_wait", "lbm_particles", "lbm_particle_forces", "lbm_checks", "lbm_step_count",
-    "lbm_save", "lbm_load", "lbm_autotune", "lbm_set_launch", "lbm_get_launch", "lbm_profile_steps", "lbm_time_stream",
+    "lbm_save", "lbm_load", "lbm_autotune", "lbm_set_launch", "lbm_get_launch", "lbm_profile_steps", "lbm_time_stream", "lbm_fp64_fma_rate",
     "lbm_checks_noalloc", "lbm_last_error", "lbm_destroy",
 ]
 NOALLOC_MAX_ROWS = 16384
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
             "lbm_get_launch": (ctypes.c_int, [_vp, _P(ctypes.c_int64)]),
             "lbm_profile_steps": (ctypes.c_int, [_vp, ctypes.c_int64, _dp, _P(ctypes.c_int64)]),
             "lbm_time_stream": (ctypes.c_int, [_vp, ctypes.c_int32, _dp]),
+            "lbm_fp64_fma_rate": (ctypes.c_int, [_vp, _dp]),
             "lbm_checks_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                   ctypes.c_int32, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp]),
             "lbm_last_error": (ctypes.c_char_p, [_vp]),
@@ -310,3 +311,13 @@ def checks_noalloc(d_populations, store, nx, ny, pitch, rho0, store_scale, d_sol
     return L.lbm_checks_noalloc(ptr(d_populations), st, int(nx), int(ny), int(pitch), float(rho0),
                                 float(store_scale), ptr(d_solid), ptr(d_out3),
                                 ctypes.c_void_p(stream) if stream else None)
+
+
+def fp64_fma_rate(stream=None):
+    """lbm_fp64_fma_rate: the device's FP64 FMA rate in GFLOP/s (2 flops per FMA)."""
+    L = load()
+    g = ctypes.c_double(0.0)
+    r = L.lbm_fp64_fma_rate(ctypes.c_void_p(stream) if stream else None, ctypes.byref(g))
+    if r != 0:
+        raise LbmError(r, (L.lbm_last_error(None) or b"").decode())
+    return float(g.value)

@@ -47,3 +47,4 @@ def test_invalid_parameters_rejected_without_gpu():
     assert L.lbm_set_launch(None, 2, 128, 2) == -1
     assert L.lbm_get_launch(None, None) == -1
     assert L.lbm_time_stream(None, 4, None) == -1
+    assert L.lbm_fp64_fma_rate(None, None) == -1

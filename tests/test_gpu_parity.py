@@ -312,3 +312,10 @@ def test_full_size_porous_workload(errlog):
         else:
             assert np.array_equal(f, first), launch
         ctx.close()
+
+
+def test_fp64_rate_probe():
+    """The FP64 rate probe that sets the FP64 store's arithmetic roofline runs and
+    reports a rate between a plausible floor and the FP32 rate of the part."""
+    g = lbm.fp64_fma_rate()
+    assert 50.0 < g < 1e5, g
