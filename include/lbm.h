@@ -184,8 +184,9 @@ int lbm_autotune(lbm_ctx* ctx, int trial_steps);
  * warps per SM, 2 staged through shared memory with bulk asynchronous copies
  * (`stages` row segments in flight per warp, 1..8; block at most 256
  * threads), 3 register kernel on a grid-stride grid of only the CTAs that fit
- * the SMs at once.  block: threads per CTA, a multiple of 32, at most
- * 128 for kernels 0, 1 and 3.  LBM_E_INVAL for values out of range
+ * the SMs at once, 4 the same on half the grid of kernel 1 (8 CTAs' worth of
+ * warps per SM).  block: threads per CTA, a multiple of 32, at most
+ * 128 for kernels 0, 1, 3 and 4.  LBM_E_INVAL for values out of range
  * or a staged configuration whose shared memory does not fit an SM; the
  * previous configuration then stays.  lbm_get_launch writes {kernel, block,
  * stages, grid} to out4. */

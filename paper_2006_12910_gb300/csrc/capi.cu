@@ -97,7 +97,8 @@ struct lbm_ctx {
     int64_t steps = 0;
     int block = 128;
     // 0: one warp item per warp; 1: grid-stride over 16 CTAs per SM; 2: staged
-    // kernel; 3: grid-stride over the CTAs that fit the SMs at once
+    // kernel; 3: grid-stride over the CTAs that fit the SMs at once; 4:
+    // grid-stride over 8 CTAs per SM
     int grid_mode = 1;
     int stages = 0;     // row segments in flight per warp of the staged kernel
     int64_t grid = 1;
@@ -172,6 +173,13 @@ void fill_dom(DomDev& D, const lbm_params& p, int kind) {
     D.plane = (int64_t)D.pitch * (p.ny + (p.walls_y ? 2 : 0));
     const int nchunks = (p.nx + D.V - 1) / D.V;
     D.seg_per_row = (nchunks + 31) / 32;
+    // Division by the invariant seg_per_row as a multiply-high (Granlund and
+    // Montgomery, PLDI 1994): with m = floor(2^32 / d) + 1, floor(n m / 2^32)
+    // = floor(n / d) whenever n d < 2^32, here for every item n of the domain.
+    {
+        const uint64_t d = (uint64_t)D.seg_per_row, items = (uint64_t)p.ny * d;
+        D.spr_magic = (d > 1 && items * d < ((uint64_t)1 << 32)) ? (uint32_t)(((uint64_t)1 << 32) / d + 1) : 0u;
+    }
     D.seed = p.seed;
     D.domain_id = p.domain_id;
     D.tau = p.tau;
@@ -291,14 +299,16 @@ void set_launch(lbm_ctx* c) {
         const int64_t share = (c->total_items + max_warps - 1) / max_warps;
         const int64_t warps = (c->total_items + share - 1) / std::max<int64_t>(share, 1);
         c->grid = std::max<int64_t>(1, (warps + wpb - 1) / wpb);
-    } else if (c->grid_mode == 1 || c->grid_mode == 3) {
+    } else if (c->grid_mode == 1 || c->grid_mode == 3 || c->grid_mode == 4) {
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int64_t per_sm = std::max<int64_t>(1, 2048 / c->block);
         const int64_t resident =
             (int64_t)sms * std::max(1, reg_blocks_per_sm(c->kind, c->noise, c->pl, c->block));
-        c->grid = std::min<int64_t>(full, c->grid_mode == 1 ? (int64_t)sms * per_sm : resident);
+        const int64_t want = c->grid_mode == 1 ? (int64_t)sms * per_sm
+                             : c->grid_mode == 4 ? (int64_t)sms * std::max<int64_t>(1, per_sm / 2) : resident;
+        c->grid = std::min<int64_t>(full, want);
     } else {
         c->grid = full;
     }
@@ -371,6 +381,7 @@ cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int bloc
     a.fliptag = c->fliptag;
     a.fliptag_stride = (int64_t)std::max<size_t>(1, c->node_bytes);
     a.flipmom = c->flipmom;
+    a.dom0 = c->hd[0];
     return launch_stream_collide(c->kind, c->noise, c->pl, a, block, grid, c->grid_mode == 2 ? c->stages : 0, s);
 }
 
@@ -1320,8 +1331,8 @@ int lbm_autotune(lbm_ctx* c, int trial_steps) {
     // a grid of resident CTAs only (3) holds every SM for the whole pass: in a
     // step with particles the particle launches then wait for the pass to end
     // (measured slower there), so it is tried only without particles
-    for (int mode : {0, 1, 3})
-        if (c->np_active == 0 || mode < 2) cands.push_back({mode, 128, 0});
+    for (int mode : {0, 1, 3, 4})
+        if (c->np_active == 0 || mode != 3) cands.push_back({mode, 128, 0});
     for (Cand k : {Cand{2, 32, 1}, Cand{2, 64, 1}, Cand{2, 64, 2}, Cand{2, 128, 1}, Cand{2, 128, 2}, Cand{2, 256, 1}})
         if (staged_blocks_per_sm(c->kind, c->noise, c->pl, k.block, k.stages) > 0) cands.push_back(k);
     cudaEvent_t e0, e1;
@@ -1356,8 +1367,8 @@ int lbm_autotune(lbm_ctx* c, int trial_steps) {
 
 int lbm_set_launch(lbm_ctx* c, int32_t kernel, int32_t block, int32_t stages) {
     if (!c) return LBM_E_INVAL;
-    if (kernel < 0 || kernel > 3 || block < 32 || block > 512 || block % 32 != 0)
-        return fail(c, LBM_E_INVAL, "kernel must be 0..3 and block a multiple of 32 in [32, 512]");
+    if (kernel < 0 || kernel > 4 || block < 32 || block > 512 || block % 32 != 0)
+        return fail(c, LBM_E_INVAL, "kernel must be 0..4 and block a multiple of 32 in [32, 512]");
     if (kernel != 2 && block > REG_K1_MAX_BLOCK)
         return fail(c, LBM_E_INVAL, "the register kernel runs at most 128 threads per CTA");
     if (kernel == 2) {

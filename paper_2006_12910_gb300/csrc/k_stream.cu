@@ -32,7 +32,8 @@ template <class S, bool NOISE, bool PL>
 constexpr int k1_min_blocks() { return (!NOISE && !PL) ? S::MINB : S::MINB_EXT; }
 
 template <class S, bool NOISE, bool PL, bool FLIPS>
-__global__ void __launch_bounds__(REG_K1_MAX_BLOCK, (k1_min_blocks<S, NOISE, PL>())) k_stream_collide(StreamArgs a) {
+__global__ void __launch_bounds__(REG_K1_MAX_BLOCK, (k1_min_blocks<S, NOISE, PL>()))
+    k_stream_collide(const __grid_constant__ StreamArgs a) {
     typedef typename S::T T;
     typedef typename S::A A;
     constexpr int V = S::V;
@@ -55,22 +56,23 @@ __global__ void __launch_bounds__(REG_K1_MAX_BLOCK, (k1_min_blocks<S, NOISE, PL>
         int64_t g = w;
         int32_t mark = (int32_t)step64;
         if (a.mode == STREAM_NEAR) g = __ldg(a.near_list + (int64_t)lpar * a.total_items + w);
-        else mark = __ldg(a.mark + (int64_t)par * a.total_items + w);  // consumed after the descriptor loads
-        const int d = a.ndom == 1 ? 0 : find_domain(a.item_off, a.ndom, g);
+        else if (a.mode == STREAM_FAR || FLIPS) mark = __ldg(a.mark + (int64_t)par * a.total_items + w);
+        const bool one = a.ndom == 1;
+        const int d = one ? 0 : find_domain(a.item_off, a.ndom, g);
         const DomDev& D = a.doms[d];
-        const Geo G = load_geo(D);
+        const Geo G = one ? param_geo(a.dom0) : load_geo(D);
         const int nx = G.nx;
         const int64_t pitch = G.pitch, plane = G.plane;
         const int local = (int)(g - G.item_off);
-        const int y = local / G.spr;
+        const int y = item_row(G, local);
         const int seg = local - y * G.spr;
         const int x0 = (seg * 32 + lane) * V;
         const uint32_t word = __ldg(a.special + G.mask_off + (int64_t)y * G.spr + seg);
         const bool near_item = mark == (int32_t)step64;
         if (a.mode == STREAM_FAR && near_item) continue;
         if (x0 >= nx) continue;
-        const HotPrm<A> H = load_hot<A>(D);
-        const ExtPrm<A> X = load_ext<A, NOISE, PL>(D);
+        const HotPrm<A> H = one ? param_hot<A>(a.dom0) : load_hot<A>(D);
+        const ExtPrm<A> X = load_ext<A, NOISE, PL>(one ? a.dom0 : D);
         const T* base = src + G.off;
         T* obase = dst + G.off;
         if (x0 + V > nx) {  // ragged tail chunk

@@ -9,6 +9,7 @@
 namespace lbmk {
 
 struct StreamArgs {
+    DomDev dom0;              // copy of doms[0] in the launch parameters (read when ndom == 1)
     const DomDev* doms;
     const int64_t* item_off;  // first work item of each domain (ndom entries)
     int ndom;

@@ -186,6 +186,10 @@ template <> __device__ __forceinline__ HotPrm<float> load_hot<float>(const DomDe
     H.rho0 = b.x; H.scale = b.y; H.inv_scale = b.z; H.pad = b.w;
     return H;
 }
+// The same from a descriptor held in the launch parameters.
+template <typename A> __device__ __forceinline__ HotPrm<A> param_hot(const DomDev& D);
+template <> __device__ __forceinline__ HotPrm<float> param_hot<float>(const DomDev& D) { return D.hot_f; }
+template <> __device__ __forceinline__ HotPrm<double> param_hot<double>(const DomDev& D) { return D.hot_d; }
 template <> __device__ __forceinline__ HotPrm<double> load_hot<double>(const DomDev& D) {
     const double2* p = reinterpret_cast<const double2*>(&D.hot_d);
     const double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);

@@ -41,7 +41,10 @@ struct alignas(16) DomDev {
     int64_t off, plane, node_off, mask_off, item_off;
     int32_t seg_per_row, V;
     int32_t p0, np;           // first particle and particle count of this domain
-    int32_t n_is_one, pad0;
+    int32_t n_is_one;
+    // work item -> row: y = umulhi(local, spr_magic) when nonzero (exact for
+    // every item of the domain), else local / seg_per_row
+    uint32_t spr_magic;
     uint64_t seed;
     uint32_t domain_id, pad1;
     double tau, inv_tau, rho0, gx, gy;

@@ -27,6 +27,7 @@ struct Geo {
     int nx, ny, pitch, flags;
     int64_t off, plane, node_off, mask_off, item_off;
     int spr;  // warp segments per row
+    uint32_t magic;  // multiply-high reciprocal of spr, or 0
 };
 static_assert(offsetof(DomDev, ny) == offsetof(DomDev, nx) + 4 && offsetof(DomDev, flags) == offsetof(DomDev, nx) + 12 &&
                   offsetof(DomDev, nx) % 16 == 0, "nx..flags must form one 16-byte block");
@@ -43,7 +44,21 @@ __device__ __forceinline__ Geo load_geo(const DomDev& D) {
     G.nx = a.x; G.ny = a.y; G.pitch = a.z; G.flags = a.w;
     G.off = b.x; G.plane = b.y; G.node_off = c.x; G.mask_off = c.y; G.item_off = e.x;
     G.spr = (int)(uint32_t)(uint64_t)e.y;
+    G.magic = 0u;
     return G;
+}
+// The same from a descriptor held in the launch parameters (no memory loads).
+__device__ __forceinline__ Geo param_geo(const DomDev& D) {
+    Geo G;
+    G.nx = D.nx; G.ny = D.ny; G.pitch = D.pitch; G.flags = D.flags;
+    G.off = D.off; G.plane = D.plane; G.node_off = D.node_off; G.mask_off = D.mask_off; G.item_off = D.item_off;
+    G.spr = D.seg_per_row;
+    G.magic = D.spr_magic;
+    return G;
+}
+// Row of a domain-local work item.
+__device__ __forceinline__ int item_row(const Geo& G, int local) {
+    return G.magic ? (int)__umulhi((uint32_t)local, G.magic) : local / G.spr;
 }
 
 // Rows that row y pulls from: y -/+ 1, wrapped when periodic in y; with y

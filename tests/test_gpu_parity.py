@@ -285,8 +285,8 @@ def test_full_size_porous_workload(errlog):
     """The benchmark workload at full size (2048x1024, ~300 obstacles, 20 particles,
     Zou-He ends, FP32 shifted store), 10 steps, every node compared with the
     oracle, on each launch shape the benchmark's autotuner may pick for the
-    register kernel (one item per warp, grid-stride, resident-only grid); the
-    three must agree bit for bit."""
+    register kernel (one item per warp, grid-stride over 16 or 8 CTAs per SM,
+    resident-only grid); all must agree bit for bit."""
     w = workloads.porous()
     base = dict(nx=w.nx, ny=w.ny, **w.params)
     f0 = np.empty((9, w.ny, w.nx))
@@ -295,7 +295,7 @@ def test_full_size_porous_workload(errlog):
     oracle.set_threads(0)
     ref.step(10)
     first = None
-    for launch in [(1, 128, 0), (0, 128, 0), (3, 128, 0)]:
+    for launch in [(1, 128, 0), (0, 128, 0), (3, 128, 0), (4, 128, 0)]:
         if first is not None:
             _, ctx = pair(base, "f32s", solid=w.solid, particles=w.particles, f0=f0)
         ctx.set_launch(*launch)
