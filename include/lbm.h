@@ -150,7 +150,13 @@ int lbm_moments_async(lbm_ctx* ctx, int dom);
 int lbm_moments_async_wait(lbm_ctx* ctx, float* rho, float* ux, float* uy);
 
 /* Particle state of domain dom at the current step (up to cap entries).
- * Returns the particle count (>= 0) or an error. Blocking. */
+ * Returns the particle count (>= 0) or an error. Blocking.  After lbm_step it
+ * waits only until the step's particle force launch has written the state
+ * (the rest of the step keeps running on the device) and copies it through a
+ * side stream; device error bits of that step are then reported by the next
+ * call that synchronises the whole context (lbm_sync, lbm_moments,
+ * lbm_checks, ...).  Otherwise (after set-up, lbm_load or lbm_profile_steps)
+ * it synchronises the context stream and reports its error bits. */
 int lbm_particles(lbm_ctx* ctx, int dom, lbm_particle* out, int cap);
 
 /* Force and torque terms of the last step for particle i of domain dom, 13

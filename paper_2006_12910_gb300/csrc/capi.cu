@@ -89,6 +89,12 @@ struct lbm_ctx {
     double2* ljwall = nullptr;           // per node: Eq. MP2 force from walls / solids (domains with psi > 0)
     int32_t* lj_cnt = nullptr;           // [ndom]
     cudaEvent_t ev_snap = nullptr, ev_copied = nullptr;
+    // Recorded inside every step graph right after the last particle force
+    // launch (which writes the particle state of the graph's last step).
+    // pstate_evt: the latest write of the particle state that was enqueued is
+    // that launch, so lbm_particles may wait for this event alone.
+    cudaEvent_t ev_pstate = nullptr;
+    bool pstate_evt = false;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // GRAPH_STEPS steps from state 0 / 1
     cudaGraphExec_t gexec1[2] = {nullptr, nullptr};  // one step from state 0 / 1
     bool graph_dirty = true;
@@ -433,6 +439,8 @@ cudaError_t enqueue_graph_chains(lbm_ctx* c, int k, int nsteps, cudaStream_t s) 
         if ((e = cudaEventRecord(c->ev_far[st & 1], c->far_stream)) != cudaSuccess) return e;
         if (st > 1 && (e = cudaStreamWaitEvent(s, c->ev_lj[st & 1], 0)) != cudaSuccess) return e;  // sums of st
         if ((e = launch_particle_step(c->kind, a, PL_STEP_A, s)) != cudaSuccess) return e;
+        if (st == nsteps - 1 && (e = cudaEventRecordWithFlags(c->ev_pstate, s, cudaEventRecordExternal)) != cudaSuccess)
+            return e;
         if ((e = cudaEventRecord(c->ev_a[st & 1], s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(c->lj_stream, c->ev_a[st & 1], 0)) != cudaSuccess) return e;
         if ((e = launch_particle_step(c->kind, a, PL_STEP_LJ, c->lj_stream)) != cudaSuccess) return e;
@@ -463,6 +471,8 @@ int capture_steps(lbm_ctx* c, int k, int nsteps, cudaGraphExec_t* out) {
     if (c->np_active > 0 && c->overlap) e = enqueue_graph_chains(c, k, nsteps, c->cap_stream);
     else
         for (int s = 0; s < nsteps && e == cudaSuccess; ++s) e = enqueue_step(c, k ^ (s & 1), c->cap_stream);
+    if (e == cudaSuccess && c->np_active > 0 && !c->overlap)
+        e = cudaEventRecordWithFlags(c->ev_pstate, c->cap_stream, cudaEventRecordExternal);
     cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
     if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); CKC(c, e); }
     CKC(c, e2);
@@ -689,6 +699,7 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
         CKCR(cudaStreamSynchronize(c->stream));
     }
     CKCR(cudaEventCreateWithFlags(&c->ev_snap, cudaEventDisableTiming));
+    CKCR(cudaEventCreateWithFlags(&c->ev_pstate, cudaEventDisableTiming));
     CKCR(cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming));
     CKCR(cudaMalloc(&c->f[0], c->arena_elems * c->esz));
     CKCR(cudaMalloc(&c->f[1], c->arena_elems * c->esz));
@@ -768,6 +779,7 @@ void lbm_destroy(lbm_ctx* c) {
     if (c->rast_stream) cudaStreamDestroy(c->rast_stream);
     if (c->lj_stream) cudaStreamDestroy(c->lj_stream);
     if (c->ev_snap) cudaEventDestroy(c->ev_snap);
+    if (c->ev_pstate) cudaEventDestroy(c->ev_pstate);
     if (c->ev_copied) cudaEventDestroy(c->ev_copied);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -798,6 +810,7 @@ int lbm_set_geometry(lbm_ctx* c, int dom, const uint8_t* solid) {
 int lbm_add_particles(lbm_ctx* c, int dom, int n, const lbm_particle* p) {
     int r = check_dom(c, dom);
     if (r) return r;
+    c->pstate_evt = false;
     if (n < 0 || (n > 0 && !p)) return fail(c, LBM_E_INVAL, "bad particle array");
     if (n == 0) return LBM_OK;
     DomDev& D = c->hd[dom];
@@ -928,6 +941,7 @@ int lbm_step(lbm_ctx* c, int64_t nsteps) {
         --left;
     }
     c->steps += nsteps;
+    c->pstate_evt = c->np_active > 0;
     return LBM_OK;
 }
 
@@ -1009,10 +1023,17 @@ int lbm_particles(lbm_ctx* c, int dom, lbm_particle* out, int cap) {
     r = ensure_pin(c, sizeof(PartState) * (size_t)D.np);
     if (r) return r;
     const PartState* s = reinterpret_cast<const PartState*>(c->h_pin + PIN_HEAD);
-    CKC(c, cudaMemcpyAsync(c->h_pin + PIN_HEAD, c->pstate + (c->steps & 1) * c->np_slots + D.p0,
-                           sizeof(PartState) * D.np, cudaMemcpyDeviceToHost, c->stream));
-    r = sync_and_check(c);
-    if (r) return r;
+    const PartState* src = c->pstate + (c->steps & 1) * c->np_slots + D.p0;
+    if (c->pstate_evt) {
+        // after steps: wait only for the force launch that wrote this state
+        CKC(c, cudaStreamWaitEvent(c->side, c->ev_pstate, 0));
+        CKC(c, cudaMemcpyAsync(c->h_pin + PIN_HEAD, src, sizeof(PartState) * D.np, cudaMemcpyDeviceToHost, c->side));
+        CKC(c, cudaStreamSynchronize(c->side));
+    } else {
+        CKC(c, cudaMemcpyAsync(c->h_pin + PIN_HEAD, src, sizeof(PartState) * D.np, cudaMemcpyDeviceToHost, c->stream));
+        r = sync_and_check(c);
+        if (r) return r;
+    }
     for (int i = 0; i < D.np && i < cap && out; ++i) {
         const PartStatic& st = c->hst[D.p0 + i];
         out[i] = lbm_particle{s[i].x, s[i].y, st.R, st.rho_p, s[i].U, s[i].V, s[i].Om, s[i].th, st.fixed, 0};
@@ -1100,6 +1121,7 @@ int lbm_save(lbm_ctx* c, const char* path) {
 
 int lbm_load(lbm_ctx* c, const char* path) {
     if (!c || !path) return LBM_E_INVAL;
+    c->pstate_evt = false;
     int r = sync_and_check(c);
     if (r) return r;
     FILE* fp = fopen(path, "rb");
@@ -1198,6 +1220,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
 
 int lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double* ms_out3, int64_t* launches_out) {
     if (!c || !ms_out3 || nsteps < 0) return c ? fail(c, LBM_E_INVAL, "bad arguments") : LBM_E_INVAL;
+    c->pstate_evt = false;
     int r = sync_and_check(c);
     if (r) return r;
     // Steps are enqueued back to back in batches, an event pair around every

@@ -319,3 +319,22 @@ def test_fp64_rate_probe():
     reports a rate between a plausible floor and the FP32 rate of the part."""
     g = lbm.fp64_fma_rate()
     assert 50.0 < g < 1e5, g
+
+
+def test_particles_read_after_step_without_full_sync():
+    """lbm_particles right after lbm_step waits only for the step's force launch;
+    the state it returns equals the one read after a full synchronisation, for
+    one-step and eight-step graph launches, and matches the oracle."""
+    nx, ny = 96, 64
+    parts = [dict(x=30.2, y=30.7, R=7.3, rho_p=1.2, U=0.02, V=-0.01, Omega=0.003),
+             dict(x=70.6, y=25.1, R=6.1, rho_p=0.9, U=-0.01, V=0.0, Omega=-0.002)]
+    base = dict(nx=nx, ny=ny, periodic_x=1, periodic_y=0, walls_y=1, tau=0.8, gx=1e-5)
+    ref, ctx = pair(base, "f32s", particles=parts)
+    for n in (1, 8, 3, 16):
+        ctx.step(n)
+        early = ctx.particles()
+        ctx.sync()
+        assert ctx.particles() == early, n
+    ref.step(28)
+    pr, pg = ref.particles(), ctx.particles()
+    assert max(abs(a[k] - b[k]) for a, b in zip(pr, pg) for k in ("x", "y", "U", "V")) < 1e-6
