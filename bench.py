@@ -30,7 +30,7 @@ if ROOT not in sys.path:
 # DRAM bytes (read + write) per full stream-collide launch, from one ncu capture of the
 # current kernel version on this workload's geometry (a pass over every work item).
 # Any change to the kernel voids it.
-NCU_TRAFFIC = {("k_stream_collide", "f32s", 2048, 1024): 104.3e6}
+NCU_TRAFFIC = {("k_stream_collide", "f32s", 2048, 1024): 105.5e6}
 
 METRIC = "D2Q9 MLUPS and % HBM roofline, FP32/FP16-store vs FP64 path at stated error"
 # FP64 operations of one BGK collision with the velocity-shift force (unshifted FP64
