@@ -187,6 +187,33 @@ def run_reference(args):
     return 0
 
 
+def channel_bench(lbm, workloads, stream, steps: int):
+    """The confined-channel fluctuating workload (3000 x 41 walled channel, one R = 7.5
+    Brownian disk, kT = 5e-5, nu = 0.1; the shape of the paper's second benchmark): MLUPS
+    of the graph-replayed step, shifted FP32 store, autotuned.  Its 8.9 MB of populations
+    stay in L2, so no HBM roofline applies; its statistics are checked by the tests."""
+    import torch
+    w = workloads.confined_channel()
+    p = lbm.make_params(nx=w.nx, ny=w.ny, store="f32s", max_particles=1, **w.params)
+    ctx = lbm.Context(p, stream=stream.cuda_stream, particles=[w.particles])
+    ctx.autotune(10)
+    ctx.step(400)
+    ctx.sync()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    ctx.step(steps)
+    a1.record(stream)
+    a1.synchronize()
+    ctx.sync()
+    ms = a0.elapsed_time(a1)
+    out = {"workload": f"confined channel {w.nx}x{w.ny}: {w.note}", "nodes": w.nx * w.ny, "steps": steps,
+           "MLUPS": w.nx * w.ny * steps / (ms * 1e-3) / 1e6, "us_per_step": ms * 1e3 / steps,
+           "launch": list(ctx.launch())}
+    ctx.close()
+    return out
+
+
 def ensemble_bench(lbm, workloads, stream, steps32: int, steps64: int, samples: int):
     """The 96-domain fluctuating-LB ensemble (uneven sizes, per-domain Philox seed and kT,
     one R = 5 Brownian disk each): all domains in one context and one launch per step
@@ -269,6 +296,8 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=500)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-channel", action="store_true")
+    ap.add_argument("--channel-steps", type=int, default=16000)
     ap.add_argument("--ensemble-steps", type=int, default=4000)
     ap.add_argument("--launch", default=None,
                     help="stream-collide kernel,block,stages (e.g. 1,128,0); skips the autotuner")
@@ -437,6 +466,11 @@ def main():
         from paper_2006_12910_gb300 import workloads as _wl
         ens = ensemble_bench(lbm, _wl, stream, args.ensemble_steps, max(100, args.ensemble_steps // 20), 20)
 
+    chan = None
+    if rank == 0 and not args.no_channel:
+        from paper_2006_12910_gb300 import workloads as _wl
+        chan = channel_bench(lbm, _wl, stream, args.channel_steps)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, t, cores = cpu_oracle_mlups(w, budget_s=15.0)
@@ -454,7 +488,7 @@ def main():
                            "launch": {"kernel": k1_name, "block": launch[1], "stages": launch[2],
                                       "grid": launch[3], "graph_steps": 8}},
                 "clocks": clk, "gpu_launches": args.steps * kernels_per_step,
-                "roofline": roofline, "e2e": e2e, "variants": variants, "ensemble": ens, "cpu_baseline": cpu}
+                "roofline": roofline, "e2e": e2e, "variants": variants, "ensemble": ens, "channel": chan, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

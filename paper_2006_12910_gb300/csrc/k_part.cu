@@ -548,7 +548,17 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
                 }
                 next_position(D, q, false, n.x, n.y);
                 n.th = q.th + q.Om;
-                if (fabs(q.U) >= 1.0 || fabs(q.V) >= 1.0) atomicOr(a.err, ERR_STATE);  // faster than a node per step
+                // A particle faster than a node per step, or a state that is no
+                // longer finite (an unstable lattice around it), is an error; the
+                // particle then stays where it was, at rest, so that later
+                // launches keep rasterising a finite disk inside the domain.
+                const bool ok = fabs(n.U) < 1.0 && fabs(n.V) < 1.0 && fabs(n.Om) < 1.0 && isfinite(n.x) &&
+                                isfinite(n.y) && isfinite(n.th);
+                if (!ok) {
+                    atomicOr(a.err, ERR_STATE);
+                    n = q;
+                    n.U = n.V = n.Om = 0.0;
+                }
             }
             a.state[(int64_t)(par ^ 1) * a.np + p] = n;
         }

@@ -163,6 +163,21 @@ def flb(nx: int = 512, ny: int = 512, seed: int = BASE_SEED + 3, R: float = 5.0,
                     f"periodic FLB kT={kT}, one R={R} disk")
 
 
+def confined_channel(nx: int = 3000, ny: int = 41, seed: int = BASE_SEED + 6, R: float = 7.5,
+                     kT: float = 5e-5, nu: float = 0.1, rho_p: float = 1.05) -> Workload:
+    """Fluctuating fluid at rest in a narrow walled channel with one disk
+    released on the centre line: the shape of the paper's second benchmark
+    (3000 x 41, R = 7.5, kT = 5e-5, nu = 0.1, no external force).  The paper
+    gives no particle density there; the disk takes the density ratio of its
+    first benchmark, 1.05."""
+    parts = [dict(x=nx / 2 + 0.3, y=(ny - 1) / 2.0 + 0.1, R=R, rho_p=rho_p, U=0.0, V=0.0, Omega=0.0, theta=0.0,
+                  fixed=0)] if R > 0 else []
+    return Workload("confined_channel", nx, ny,
+                    dict(periodic_x=1, periodic_y=0, walls_y=1, inlet_outlet=0, tau=0.5 + 3.0 * nu, rho0=1.0,
+                         gx=0.0, gy=0.0, kT=kT, seed=seed, lj_psi=LJ_PSI, lj_rit=2.5), None, parts, 800000,
+                    f"walled channel FLB kT={kT} nu={nu}, one R={R} disk rho_p={rho_p} on the centre line")
+
+
 def power_law(n: float, nx: int = 4096, ny: int = 256, g: float = 1e-6, xi: float = 0.01) -> Workload:
     return Workload(f"power_law_n{n}", nx, ny,
                     dict(periodic_x=1, periodic_y=0, walls_y=1, inlet_outlet=0, tau=1.0, rho0=1.0,

@@ -107,3 +107,25 @@ def test_equipartition_of_every_mode(oracle, tau):
         acc.append(np.concatenate([[((f.sum(0) - 1) ** 2).mean()], (m[1:] ** 2).mean(1)]))
     ratio = np.mean(acc, axis=0) / (3 * kT)
     assert np.abs(ratio - 1).max() < 0.02
+
+
+def test_thermalisation_in_walled_channel(oracle):
+    """A fluctuating fluid at rest between halfway bounce-back walls thermalises
+    row by row, wall rows included (Sec. 4; the confined-channel result the paper
+    recalls for its second benchmark): <j_x^2> = <j_y^2> = rho kT and
+    <drho^2> = rho kT / c_s^2 on every row."""
+    nx, ny, kT = 64, 17, 1e-4
+    d = oracle.Domain(oracle.make_params(nx=nx, ny=ny, tau=0.8, kT=kT, seed=4321, periodic_x=1, periodic_y=0,
+                                         walls_y=1))
+    d.step(500)
+    acc = []
+    for _ in range(400):
+        d.step(10)
+        f = d.populations().reshape(9, ny, nx)
+        jx = (f[1] + f[5] + f[8]) - (f[3] + f[6] + f[7])
+        jy = (f[2] + f[5] + f[6]) - (f[4] + f[7] + f[8])
+        acc.append([(jx ** 2).mean(axis=1), (jy ** 2).mean(axis=1), ((f.sum(0) - 1.0) ** 2).mean(axis=1) / 3])
+    rows = np.mean(acc, axis=0) / kT  # [quantity][row]
+    # each row averages 64 nodes x 400 samples: about 1 % standard error per row
+    assert np.abs(rows - 1).max() < 0.05, rows
+    assert np.abs(rows.mean(axis=1) - 1).max() < 0.015, rows.mean(axis=1)
