@@ -214,6 +214,43 @@ def channel_bench(lbm, workloads, stream, steps: int):
     return out
 
 
+def combined_bench(lbm, workloads, stream, steps: int, peak: float):
+    """Every feature at once on the benchmark geometry (2048 x 1024 porous workload with
+    its particles, plus a power-law fluid n = 0.75 and thermal noise kT = 1e-5): the HBM
+    fraction of the stream-collide pass (its variant with noise and tau*) and MLUPS of the
+    graph-replayed step, shifted FP32 store, autotuned.  This combination turns unstable
+    after a few hundred steps (particles with the power law and noise together; each pair
+    alone is stable), so the step is timed over a short window from rest and an instability
+    inside it is reported instead of a number."""
+    import torch
+    w = workloads.combined()
+    fluid = int((w.solid == 0).sum())
+    p = lbm.make_params(nx=w.nx, ny=w.ny, store="f32s", max_particles=len(w.particles), **w.params)
+    ctx = lbm.Context(p, stream=stream.cuda_stream, solids=[w.solid], particles=[w.particles])
+    out = {"workload": f"combined {w.nx}x{w.ny}: {w.note}", "nodes": w.nx * w.ny, "steps": steps}
+    try:
+        ctx.autotune(10)
+        ctx.step(16)
+        ctx.sync()
+        k1 = ctx.time_stream(100) / 100
+        gbs = fluid * 72 / (k1 * 1e-3) / 1e9
+        out.update(kernel_ms=k1, kernel_GBs=gbs, frac=gbs / peak)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        ctx.step(steps)
+        a1.record(stream)
+        a1.synchronize()
+        ctx.sync()
+        ms = a0.elapsed_time(a1)
+        out.update(MLUPS=w.nx * w.ny * steps / (ms * 1e-3) / 1e6, us_per_step=ms * 1e3 / steps,
+                   launch=list(ctx.launch()))
+    except lbm.LbmError as e:
+        out["error"] = str(e)
+    ctx.close()
+    return out
+
+
 def ensemble_bench(lbm, workloads, stream, steps32: int, steps64: int, samples: int):
     """The 96-domain fluctuating-LB ensemble (uneven sizes, per-domain Philox seed and kT,
     one R = 5 Brownian disk each): all domains in one context and one launch per step
@@ -297,6 +334,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-channel", action="store_true")
+    ap.add_argument("--no-combined", action="store_true")
     ap.add_argument("--channel-steps", type=int, default=16000)
     ap.add_argument("--ensemble-steps", type=int, default=4000)
     ap.add_argument("--launch", default=None,
@@ -471,6 +509,11 @@ def main():
         from paper_2006_12910_gb300 import workloads as _wl
         chan = channel_bench(lbm, _wl, stream, args.channel_steps)
 
+    comb = None
+    if rank == 0 and not args.no_combined:
+        from paper_2006_12910_gb300 import workloads as _wl
+        comb = combined_bench(lbm, _wl, stream, 200, peak)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, t, cores = cpu_oracle_mlups(w, budget_s=15.0)
@@ -488,7 +531,7 @@ def main():
                            "launch": {"kernel": k1_name, "block": launch[1], "stages": launch[2],
                                       "grid": launch[3], "graph_steps": 8}},
                 "clocks": clk, "gpu_launches": args.steps * kernels_per_step,
-                "roofline": roofline, "e2e": e2e, "variants": variants, "ensemble": ens, "channel": chan, "cpu_baseline": cpu}
+                "roofline": roofline, "e2e": e2e, "variants": variants, "ensemble": ens, "channel": chan, "combined": comb, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

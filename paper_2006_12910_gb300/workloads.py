@@ -185,6 +185,18 @@ def power_law(n: float, nx: int = 4096, ny: int = 256, g: float = 1e-6, xi: floa
                     None, [], 2000, f"power-law channel n={n} xi={xi} g={g}")
 
 
+def combined(nx: int = 2048, ny: int = 1024, n_pl: float = 0.75, xi: float = 0.01, kT: float = 1e-5,
+             seed: int = BASE_SEED + 7) -> Workload:
+    """Every feature at once, the combination the paper names as untested: the
+    porous workload's obstacles, particles and density-driven flow, with a
+    power-law fluid (n, xi; tau* clamped to [0.51, 2.0]) and thermal noise."""
+    w = porous(nx, ny)
+    w.name = "combined"
+    w.params.update(power_law=1, n_pl=n_pl, xi_pl=xi, tau_min=0.51, tau_max=2.0, kT=kT, seed=seed)
+    w.note += f", power law n={n_pl} xi={xi}, kT={kT}"
+    return w
+
+
 ENSEMBLE_SIZES = ((128, 128), (256, 128), (384, 256), (512, 512))
 
 
