@@ -214,6 +214,36 @@ def channel_bench(lbm, workloads, stream, steps: int):
     return out
 
 
+def grains_bench(lbm, workloads, stream, steps: int, peak: float):
+    """The paper's first-benchmark shape (1620 x 1020 grains, periodic along the flow,
+    walls across, diagonal force, 45 disks of radius 6.5 released near the inlet): MLUPS
+    of the graph-replayed step and the HBM fraction of the stream-collide pass, shifted
+    FP32 store, autotuned."""
+    import torch
+    w = workloads.grains()
+    fluid = int((w.solid == 0).sum())
+    p = lbm.make_params(nx=w.nx, ny=w.ny, store="f32s", max_particles=len(w.particles), **w.params)
+    ctx = lbm.Context(p, stream=stream.cuda_stream, solids=[w.solid], particles=[w.particles])
+    ctx.autotune(10)
+    ctx.step(200)
+    ctx.sync()
+    k1 = ctx.time_stream(100) / 100
+    gbs = fluid * 72 / (k1 * 1e-3) / 1e9
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    ctx.step(steps)
+    a1.record(stream)
+    a1.synchronize()
+    ctx.sync()
+    ms = a0.elapsed_time(a1)
+    out = {"workload": f"grains {w.nx}x{w.ny}: {w.note}", "nodes": w.nx * w.ny, "fluid_nodes": fluid,
+           "steps": steps, "MLUPS": w.nx * w.ny * steps / (ms * 1e-3) / 1e6, "us_per_step": ms * 1e3 / steps,
+           "kernel_ms": k1, "kernel_GBs": gbs, "frac": gbs / peak, "launch": list(ctx.launch())}
+    ctx.close()
+    return out
+
+
 def combined_bench(lbm, workloads, stream, steps: int, peak: float):
     """Every feature at once on the benchmark geometry (2048 x 1024 porous workload with
     its particles, plus a power-law fluid n = 0.75 and thermal noise kT = 1e-5): the HBM
@@ -335,6 +365,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-channel", action="store_true")
     ap.add_argument("--no-combined", action="store_true")
+    ap.add_argument("--no-grains", action="store_true")
     ap.add_argument("--channel-steps", type=int, default=16000)
     ap.add_argument("--ensemble-steps", type=int, default=4000)
     ap.add_argument("--launch", default=None,
@@ -509,6 +540,11 @@ def main():
         from paper_2006_12910_gb300 import workloads as _wl
         chan = channel_bench(lbm, _wl, stream, args.channel_steps)
 
+    grains = None
+    if rank == 0 and not args.no_grains:
+        from paper_2006_12910_gb300 import workloads as _wl
+        grains = grains_bench(lbm, _wl, stream, 4000, peak)
+
     comb = None
     if rank == 0 and not args.no_combined:
         from paper_2006_12910_gb300 import workloads as _wl
@@ -531,7 +567,7 @@ def main():
                            "launch": {"kernel": k1_name, "block": launch[1], "stages": launch[2],
                                       "grid": launch[3], "graph_steps": 8}},
                 "clocks": clk, "gpu_launches": args.steps * kernels_per_step,
-                "roofline": roofline, "e2e": e2e, "variants": variants, "ensemble": ens, "channel": chan, "combined": comb, "cpu_baseline": cpu}
+                "roofline": roofline, "e2e": e2e, "variants": variants, "ensemble": ens, "channel": chan, "grains": grains, "combined": comb, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

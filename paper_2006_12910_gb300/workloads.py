@@ -197,6 +197,37 @@ def combined(nx: int = 2048, ny: int = 1024, n_pl: float = 0.75, xi: float = 0.0
     return w
 
 
+def grains(nx: int = 1620, ny: int = 1020, n_obstacles: int = 236, seed: int = BASE_SEED + 8,
+           release_x: float = 100.0) -> Workload:
+    """The shape of the paper's first benchmark, turned so that the flow runs along x:
+    a 1620-long periodic direction (inlet and outlet) between no-flow walls 1020
+    apart, a Newtonian fluid with nu = 0.136 (tau = 0.908) driven by a diagonal body
+    force (1e-5 along the flow, 1e-6 across), seeded disk grains R ~ U[8, 24] with a
+    surface gap of 4 outside the release zone x < release_x, and 45 disks of radius
+    6.5 (density ratio 1.05) released at rest near the inlet in two closely packed
+    arrays: 23 and 22 disks across the channel with surface gaps of 8.5 between
+    neighbours and 5.5 between the arrays (fewer when the channel is narrower)."""
+    R = 6.5
+    obstacles = [d for d in place_obstacles(nx, ny, n_obstacles, 8.0, 24.0, gap=4.0, margin_y=2.0, margin_x=6.0,
+                                            seed=seed) if d[0] - d[2] > release_x]
+    solid = disk_mask(nx, ny, obstacles)
+    parts = []
+    x0 = 40.0
+    fit = int((ny - 2 * (R + 4.0)) // (2 * R + 8.5)) + 1  # disks that fit across a narrower channel
+    for row, count in ((0, min(23, fit)), (1, min(22, fit - 1))):
+        x = x0 + row * (2 * R + 5.5)
+        span = (count - 1) * (2 * R + 8.5)
+        for k in range(count):
+            y = (ny - 1) / 2.0 - span / 2.0 + k * (2 * R + 8.5) + 0.25
+            parts.append(dict(x=x, y=y, R=R, rho_p=1.05, U=0.0, V=0.0, Omega=0.0, theta=0.0, fixed=0))
+    return Workload("grains", nx, ny,
+                    dict(periodic_x=1, periodic_y=0, walls_y=1, inlet_outlet=0, tau=0.5 + 3 * 0.136, rho0=1.0,
+                         gx=1e-5, gy=1e-6, lj_psi=LJ_PSI, lj_rit=2.5),
+                    solid, parts, 56000,
+                    f"{len(obstacles)} grains R~U[8,24] gap 4, {len(parts)} disks R=6.5 rho_p=1.05 released near the inlet, "
+                    f"diagonal force (1e-5, 1e-6), periodic along the flow, walls across")
+
+
 ENSEMBLE_SIZES = ((128, 128), (256, 128), (384, 256), (512, 512))
 
 
