@@ -84,6 +84,8 @@ typedef struct {
     int32_t store;             /* lbm_store; must be the same for every domain */
     int32_t max_particles;     /* capacity reserved for lbm_add_particles */
     double store_scale;        /* power-of-two scale of the shifted FP16/BF16 store */
+    double kappa_pl;           /* kappa of Eq. nn4 (Sec. 5 cites 0.5^(n-1), 1 and 2^(n-1));
+                                  0 takes 2^(n-1), the value the paper adopts */
 } lbm_params;
 
 /* A rigid circular particle (Sec. 3).  Position in lattice units with node

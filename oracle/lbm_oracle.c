@@ -215,7 +215,12 @@ void or_collide_node(const or_params* p, const double* f, double* out, uint32_t 
     double tau = p->tau;
     if (p->power_law) {
         const double A = or_strain_A(f, rho, jx, jy);
-        tau = or_solve_tau(A, p->n_pl, p->xi_pl, p->tau_min, p->tau_max);
+        /* Eq. (nn4) with another kappa: nu* = xi kappa |Pi_D|^((n-1)/2)
+         * = (xi kappa / 2^(n-1)) (A/tau)^(n-1), i.e. the solve below with the
+         * consistency scaled by kappa / 2^(n-1). */
+        double xi = p->xi_pl;
+        if (p->kappa_pl > 0.0) xi *= p->kappa_pl / pow(2.0, p->n_pl - 1.0);
+        tau = or_solve_tau(A, p->n_pl, xi, p->tau_min, p->tau_max);
     }
     const double ux = (jx + tau * rho * p->gx) / rho;
     const double uy = (jy + tau * rho * p->gy) / rho;

@@ -48,6 +48,7 @@ typedef struct {
     int32_t power_law;             /* 1 enables Sec. 5 */
     double n_pl, xi_pl, tau_min, tau_max;
     double lj_psi, lj_rit;         /* Eq. (MP2) stiffness and threshold */
+    double kappa_pl;               /* kappa of Eq. (nn4); 0 means 2^(n-1) */
 } or_params;
 
 typedef struct {

@@ -54,6 +54,7 @@ class Params(ctypes.Structure):
         ("power_law", ctypes.c_int32), ("n_pl", ctypes.c_double), ("xi_pl", ctypes.c_double),
         ("tau_min", ctypes.c_double), ("tau_max", ctypes.c_double),
         ("lj_psi", ctypes.c_double), ("lj_rit", ctypes.c_double),
+        ("kappa_pl", ctypes.c_double),
     ]
 
 
@@ -125,7 +126,7 @@ def make_params(**kw) -> Params:
     d = dict(nx=16, ny=16, periodic_x=1, periodic_y=1, walls_y=0, inlet_outlet=0,
              tau=0.8, rho0=1.0, gx=0.0, gy=0.0, rho_in=1.0, rho_out=1.0, kT=0.0, seed=0,
              domain_id=0, power_law=0, n_pl=1.0, xi_pl=0.1, tau_min=0.5 + 1e-9,
-             tau_max=1e9, lj_psi=0.0, lj_rit=2.5)
+             tau_max=1e9, lj_psi=0.0, lj_rit=2.5, kappa_pl=0.0)
     d.update(kw)
     return Params(**d)
 

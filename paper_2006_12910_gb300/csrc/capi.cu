@@ -157,6 +157,7 @@ int validate(const lbm_params& p, int d, lbm_ctx* c) {
     if (p.inlet_outlet && (!(p.rho_in > 0.0) || !(p.rho_out > 0.0))) return bad("rho_in / rho_out must be > 0");
     if (p.power_law) {
         if (!(p.n_pl > 0.0) || !(p.xi_pl > 0.0)) return bad("power law needs n > 0 and xi > 0");
+        if (!(p.kappa_pl >= 0.0)) return bad("kappa_pl must be >= 0 (0: 2^(n-1))");
         if (!(p.tau_min > 0.5) || !(p.tau_max > p.tau_min)) return bad("power law needs 1/2 < tau_min < tau_max");
     }
     if (p.max_particles < 0 || p.max_particles > 4096) return bad("max_particles must be in [0, 4096]");
@@ -200,7 +201,11 @@ void fill_dom(DomDev& D, const lbm_params& p, int kind) {
     D.drho_out = shifted ? p.rho_out - p.rho0 : p.rho_out;
     D.kT = p.kT;
     D.n_pl = p.power_law ? p.n_pl : 1.0;
+    // Eq. nn4, nu* = xi kappa |Pi_D|^((n-1)/2) with gamma-dot = 2 sqrt|Pi_D|, is
+    // xi kappa 2^(1-n) gamma-dot^(n-1): the kernels take the consistency times
+    // kappa / 2^(n-1) (1 for the paper's kappa = 2^(n-1)).
     D.xi_pl = p.xi_pl;
+    if (p.power_law && p.kappa_pl > 0.0) D.xi_pl = p.xi_pl * p.kappa_pl / std::pow(2.0, p.n_pl - 1.0);
     D.tau_min = p.tau_min;
     D.tau_max = p.tau_max;
     D.n_is_one = p.power_law ? (p.n_pl == 1.0) : 1;

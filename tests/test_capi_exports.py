@@ -25,8 +25,10 @@ def test_every_declared_symbol_is_exported():
 
 def test_param_struct_layout_matches_header():
     from paper_2006_12910_gb300 import lbm
-    # 6 int32, 6 double, kT, seed, domain_id + power_law, 6 doubles, store + max_particles, store_scale
-    assert ctypes.sizeof(lbm.Params) == 24 + 48 + 8 + 8 + 8 + 48 + 8 + 8
+    # 6 int32, 6 double, kT, seed, domain_id + power_law, 6 doubles, store + max_particles, store_scale,
+    # kappa_pl
+    assert ctypes.sizeof(lbm.Params) == 24 + 48 + 8 + 8 + 8 + 48 + 8 + 8 + 8
+    assert lbm.Params.kappa_pl.offset == 160
     assert ctypes.sizeof(lbm.Particle) == 8 * 8 + 8
 
 

@@ -118,6 +118,36 @@ def test_power_law_channel(store, n, errlog):
     assert_close(errs, tols, f"{store} n={n}")
 
 
+@pytest.mark.parametrize("store", ["f64", "f32s"])
+@pytest.mark.parametrize("variant", ["kappa=1", "kappa=0.5^(n-1)", "nu in [1e-5, 0.1]"])
+@pytest.mark.parametrize("n", [0.75, 1.5])
+def test_power_law_paper_variants(store, variant, n, errlog):
+    """The other kappa values of Eq. nn4 that Sec. 5 cites, and the paper's own
+    bounds on nu* (1e-5 <= nu* <= 0.1, i.e. tau* in [0.50003, 0.8]), on the
+    developed channel start of test_power_law_channel."""
+    nx, ny = 64, 32
+    base = dict(nx=nx, ny=ny, periodic_x=1, periodic_y=0, walls_y=1, tau=1.0, gx=2e-5, power_law=1,
+                n_pl=n, xi_pl=0.01, tau_min=0.51, tau_max=2.0)
+    if variant == "kappa=1":
+        base["kappa_pl"] = 1.0
+    elif variant == "kappa=0.5^(n-1)":
+        base["kappa_pl"] = 0.5 ** (n - 1)
+    else:
+        base.update(tau_min=0.5 + 3 * 1e-5, tau_max=0.5 + 3 * 0.1)
+    Y = np.arange(ny) + 0.5
+    u = 4e-3 * Y * (ny - Y) / (ny / 2) ** 2
+    f0 = np.zeros((9, ny, nx))
+    for y in range(ny):
+        f0[:, y, :] = oracle.feq(1.0, u[y], 0.0)[:, None]
+    f0 *= 1 + 1e-4 * np.sin(2 * np.pi * np.arange(nx) / nx)[None, None, :]
+    ref, ctx = pair(base, store, f0=f0)
+    ref.step(300)
+    ctx.step(300)
+    errs, tols = compare_state(ref, ctx, store)
+    errlog(store=store, variant=variant, n=n, **errs)
+    assert_close(errs, tols, f"{store} {variant} n={n}")
+
+
 @pytest.mark.parametrize("store", STORES)
 @pytest.mark.parametrize("tau", [1.0, 0.8])
 def test_fluctuating_lb_10_steps_pointwise(store, tau, errlog):

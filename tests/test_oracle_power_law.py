@@ -89,3 +89,35 @@ def test_channel_profile_matches_nn6_nn7(oracle, n, xi, g):
             break
         last = prof.copy()
     assert np.abs(prof - prof0).max() / u0 < 1e-2
+
+
+@pytest.mark.parametrize("kappa_of_n", ["0.5^(n-1)", "1", "2^(n-1)"])
+def test_kappa_variants_keep_the_normalised_profile(oracle, kappa_of_n):
+    """Eq. nn4 with each kappa Sec. 5 cites: nu* = xi kappa |Pi_D|^((n-1)/2) with
+    gamma-dot = 2 sqrt|Pi_D| is (xi kappa 2^(1-n)) gamma-dot^(n-1), so the steady
+    channel follows Eqs. nn6-nn7 with xi replaced by xi kappa 2^(1-n): the
+    amplitude u0 changes with kappa and the normalised profile u/u0 does not
+    (the paper reports that the three values perform equally well for the
+    normalised steady velocity)."""
+    n, xi, g = 0.75, 0.02, 2e-5
+    kappa = {"0.5^(n-1)": 0.5 ** (n - 1), "1": 1.0, "2^(n-1)": 2.0 ** (n - 1)}[kappa_of_n]
+    xi_eff = xi * kappa * 2.0 ** (1 - n)
+    W, nx = 32, 4
+    u0 = (g / xi_eff) ** (1 / n) * (W / 2) ** (1 + 1 / n) * n / (n + 1)
+    Yc = np.abs(np.arange(W) + 0.5 - W / 2)
+    shape = 1 - (2 * Yc / W) ** (1 + 1 / n)
+    f0 = np.zeros((9, W, nx))
+    for y in range(W):
+        f0[:, y, :] = oracle.feq(1.0, 0.98 * u0 * shape[y], 0.0)[:, None]
+    p = oracle.make_params(nx=nx, ny=W, periodic_x=1, periodic_y=0, walls_y=1, tau=1.0, gx=g,
+                           power_law=1, n_pl=n, xi_pl=xi, tau_min=0.51, tau_max=2.0, kappa_pl=kappa)
+    d = oracle.Domain(p, f0=f0)
+    last = None
+    for _ in range(100):
+        d.step(2000)
+        prof = d.moments()[1][:, 0]
+        if last is not None and np.abs(prof - last).max() < 1e-9 * prof.max():
+            break
+        last = prof.copy()
+    assert np.abs(prof - u0 * shape).max() / u0 < 1e-2
+    assert np.abs(prof / prof.max() - shape / shape.max()).max() < 1e-2
