@@ -123,10 +123,13 @@ def porous_workload(nx=2048, ny=1024):
     return workloads.porous(nx, ny)
 
 
-def cpu_oracle_mlups(w, budget_s: float, steps_hint: int | None = None):
-    """Time the FP64 oracle, as it stands, on the host cores for ~budget_s."""
+def cpu_oracle_mlups(w, budget_s: float, steps_hint: int | None = None, threads: int = 0):
+    """Time the FP64 oracle, as it stands, on the host cores (or `threads` of them) for
+    ~budget_s."""
     from oracle import oracle
     oracle.build()
+    if threads > 0:
+        oracle.set_threads(threads)
     p = oracle.make_params(nx=w.nx, ny=w.ny, **{k: v for k, v in w.params.items()
                                                  if k in {f[0] for f in oracle.Params._fields_}})
     d = oracle.Domain(p, solid=w.solid, particles=w.particles)
@@ -139,7 +142,8 @@ def cpu_oracle_mlups(w, budget_s: float, steps_hint: int | None = None):
     d.step(n)
     t = time.perf_counter() - t0
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return w.nx * w.ny * n / t / 1e6, n, t, cores
+    oracle.set_threads(cores)  # back to every core
+    return w.nx * w.ny * n / t / 1e6, n, t, (threads if threads > 0 else cores)
 
 
 def run_reference(args):
@@ -555,6 +559,9 @@ def main():
         v, n, t, cores = cpu_oracle_mlups(w, budget_s=15.0)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{n} timesteps of the full 2048x1024 porous workload, FP64 oracle, OpenMP static"}
+        v1, n1, t1, _ = cpu_oracle_mlups(w, budget_s=6.0, threads=1)
+        cpu["single_core"] = {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": f"{n1} timesteps of the same workload on one thread"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
