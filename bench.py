@@ -52,6 +52,25 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The largest of every rank's value (the job's time is its slowest rank's):
+    an all-reduce over the default process group, or x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes_per_rank: int, steps: int, ms: float, world: int) -> float:
+    """Whole-job throughput of N replicas (weak scaling): every rank advances its own
+    copy of the workload, so the job updates world x nodes per step in the slowest
+    rank's time."""
+    return world * nodes_per_rank * steps / (ms * 1e-3) / 1e6
+
+
 def _dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -439,13 +458,8 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * nodes * args.steps / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(e0.elapsed_time(e1), world, device="cuda")
+    value = job_mlups(nodes, args.steps, ms, world)
 
     # ---- per-kernel device time ----------------------------------------------------------------
     # The dominant kernel's launch duration: CUDA events on the context stream (the stream the
