@@ -137,6 +137,10 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": pmax}
 
 
+def workload_name(w) -> str:
+    return f"porous {w.nx}x{w.ny} D2Q9: {w.note}, tau={w.params['tau']}, walls y"
+
+
 def porous_workload(nx=2048, ny=1024):
     from paper_2006_12910_gb300 import workloads
     return workloads.porous(nx, ny)
@@ -187,6 +191,7 @@ def run_reference(args):
     ny = int(max(32, min(1024, round((nodes / 2) ** 0.5 / 8) * 8)))
     nx = int(max(64, min(2048, round(nodes / ny / 8) * 8)))
     w = workloads.porous(nx, ny)
+    full = porous_workload()
     p = oracle.make_params(nx=w.nx, ny=w.ny, **{k: v for k, v in w.params.items()
                                                  if k in {f[0] for f in oracle.Params._fields_}})
     d = oracle.Domain(p, solid=w.solid, particles=w.particles)
@@ -202,8 +207,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"porous {w.nx}x{w.ny} (sample of porous 2048x1024)", "nodes": w.nx * w.ny,
-                       "store": "f64 (CPU oracle)"},
+            "config": {"workload": workload_name(full), "nodes": full.nx * full.ny,
+                       "fluid_nodes": int((full.solid == 0).sum()), "store": "f64 (CPU oracle)",
+                       "sample": f"{w.nx}x{w.ny}"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -581,7 +587,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"porous {w.nx}x{w.ny} D2Q9: {w.note}, tau=0.7, walls y",
+                "config": {"workload": workload_name(w),
                            "nodes": nodes, "fluid_nodes": fluid, "store": args.store,
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                            "l2": "no flush; per-step footprint (2 arenas) exceeds the 129 MB L2",
