@@ -505,14 +505,14 @@ def main():
         ctx2.set_populations(f0.numpy())
         for _ in range(K2):
             ctx2.step(1)
-            ctx2.particles()
+            ctx2.particles_array()
         rho, ux, uy = ctx2.moments()
         t = time.perf_counter() - t0
         h2d = 9 * nodes * 8 / K2
         d2h = len(w.particles) * 64 + 3 * nodes * 8 / K2
         e2e = {"value": world * nodes * K2 / t / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": K2,
-               "what": "lbm_set_populations(pinned FP64) + K x [lbm_step(1) + lbm_particles] + lbm_moments"}
+               "what": "lbm_set_populations(pinned FP64) + K x [lbm_step(1) + lbm_particles (particles_array)] + lbm_moments"}
         ctx2.close()
 
     # ---- other storage kinds on the same workload (short) ----------------------------------

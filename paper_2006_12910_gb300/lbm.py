@@ -158,6 +158,7 @@ class Context:
         self.L = load()
         plist = params if isinstance(params, (list, tuple)) else [params]
         self.params = list(plist)
+        self._pbuf = {}
         self.ndom = len(plist)
         arr = (Params * self.ndom)(*plist)
         h = ctypes.c_void_p()
@@ -257,6 +258,20 @@ class Context:
         n = self._ck(self.L.lbm_particles(self.h, dom, arr, cap))
         keys = ("x", "y", "R", "rho_p", "U", "V", "Omega", "theta", "fixed")
         return [{k: getattr(arr[i], k) for k in keys} for i in range(n)]
+
+    def particles_array(self, dom=0):
+        """The same states as particles(), as a float64 array [n, 8] with columns x, y,
+        R, rho_p, U, V, Omega, theta: one C call into a buffer kept between calls and
+        one copy, for loops that read the particles every step."""
+        buf = self._pbuf.get(dom)
+        if buf is None:
+            cap = max(int(self.params[dom].max_particles), 1)
+            arr = (Particle * cap)()
+            view = np.frombuffer(arr, dtype=np.float64).reshape(cap, 9)  # 8 doubles + the two int32 words
+            buf = self._pbuf[dom] = (arr, view, cap)
+        arr, view, cap = buf
+        n = self._ck(self.L.lbm_particles(self.h, dom, arr, cap))
+        return view[:n, :8].copy()
 
     def particle_forces(self, i, dom=0):
         out = np.zeros(DIAG_N)

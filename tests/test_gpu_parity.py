@@ -360,11 +360,15 @@ def test_particles_read_after_step_without_full_sync():
              dict(x=70.6, y=25.1, R=6.1, rho_p=0.9, U=-0.01, V=0.0, Omega=-0.002)]
     base = dict(nx=nx, ny=ny, periodic_x=1, periodic_y=0, walls_y=1, tau=0.8, gx=1e-5)
     ref, ctx = pair(base, "f32s", particles=parts)
+    keys = ("x", "y", "R", "rho_p", "U", "V", "Omega", "theta")
     for n in (1, 8, 3, 16):
         ctx.step(n)
         early = ctx.particles()
         ctx.sync()
         assert ctx.particles() == early, n
+        arr = ctx.particles_array()
+        assert arr.shape == (len(parts), 8)
+        assert all(arr[i, j] == early[i][k] for i in range(len(parts)) for j, k in enumerate(keys))
     ref.step(28)
     pr, pg = ref.particles(), ctx.particles()
     assert max(abs(a[k] - b[k]) for a, b in zip(pr, pg) for k in ("x", "y", "U", "V")) < 1e-6
