@@ -50,3 +50,48 @@ def test_invalid_parameters_rejected_without_gpu():
     assert L.lbm_get_launch(None, None) == -1
     assert L.lbm_time_stream(None, 4, None) == -1
     assert L.lbm_fp64_fma_rate(None, None) == -1
+
+
+def _compiled_layout(tmp_path, header_dir, header, structs):
+    """sizeof and offsetof of every field of the ctypes mirrors, as the host C
+    compiler lays the C structs out."""
+    import shutil
+    import subprocess
+
+    import pytest
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = []
+    for ctype, cls in structs:
+        lines.append(f'printf("{ctype} sizeof %zu\\n", sizeof({ctype}));')
+        for name, _ in cls._fields_:
+            lines.append(f'printf("{ctype} {name} %zu\\n", offsetof({ctype}, {name}));')
+    src = tmp_path / "layout.c"
+    src.write_text(f'#include <stdio.h>\n#include <stddef.h>\n#include "{header}"\nint main(void) {{\n'
+                   + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-I", header_dir, str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)]).decode().splitlines():
+        ctype, name, value = line.split()
+        got[(ctype, name)] = int(value)
+    for ctype, cls in structs:
+        assert got[(ctype, "sizeof")] == ctypes.sizeof(cls), ctype
+        for name, _ in cls._fields_:
+            assert got[(ctype, name)] == getattr(cls, name).offset, (ctype, name)
+
+
+def test_binding_structs_match_the_header_as_compiled(tmp_path):
+    """Every field of lbm_params and lbm_particle sits at the same offset in the
+    binding's ctypes mirrors as in include/lbm.h compiled by the host C compiler."""
+    from paper_2006_12910_gb300 import lbm
+    _compiled_layout(tmp_path, os.path.join(ROOT, "include"), "lbm.h",
+                     (("lbm_params", lbm.Params), ("lbm_particle", lbm.Particle)))
+
+
+def test_oracle_structs_match_its_header_as_compiled(tmp_path):
+    """The same for the oracle's parameter and particle blocks."""
+    from oracle import oracle
+    _compiled_layout(tmp_path, os.path.join(ROOT, "oracle"), "lbm_oracle.h",
+                     (("or_params", oracle.Params), ("or_particle", oracle.Particle)))
