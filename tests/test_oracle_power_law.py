@@ -121,3 +121,53 @@ def test_kappa_variants_keep_the_normalised_profile(oracle, kappa_of_n):
         last = prof.copy()
     assert np.abs(prof - u0 * shape).max() / u0 < 1e-2
     assert np.abs(prof / prof.max() - shape / shape.max()).max() < 1e-2
+
+
+@pytest.mark.parametrize("n,xi,g", [(0.75, 0.02, 2e-5), (1.5, 2.2, 1.3e-5)])
+def test_local_strain_matches_finite_difference_gradients(oracle, n, xi, g):
+    """Cross-check of the strain reading (Eq. nn3 from the local non-equilibrium
+    moments of the populations the collision sees): in a developed power-law
+    channel, gamma-dot = A / tau* at each node equals 2 sqrt|Pi_D| with Pi_D of
+    Eq. nn3 built from central differences of the velocity field (|du/dy| here)
+    to the discretisation error of the differences, away from the walls and the
+    centre line.  The stored state is post-collision, so the test streams it
+    first (pull along y, halfway bounce-back at the walls; the channel is
+    uniform in x)."""
+    W, nx = 32, 4
+    u0 = (g / xi) ** (1 / n) * (W / 2) ** (1 + 1 / n) * n / (n + 1)
+    Yc = np.abs(np.arange(W) + 0.5 - W / 2)
+    f0 = np.zeros((9, W, nx))
+    for y in range(W):
+        f0[:, y, :] = oracle.feq(1.0, 0.98 * u0 * (1 - (2 * Yc[y] / W) ** (1 + 1 / n)), 0.0)[:, None]
+    p = oracle.make_params(nx=nx, ny=W, periodic_x=1, periodic_y=0, walls_y=1, tau=1.0, gx=g,
+                           power_law=1, n_pl=n, xi_pl=xi, tau_min=0.51, tau_max=2.0)
+    d = oracle.Domain(p, f0=f0)
+    last = None
+    for _ in range(100):
+        d.step(2000)
+        prof = d.moments()[1][:, 0]
+        if last is not None and np.abs(prof - last).max() < 1e-9 * prof.max():
+            break
+        last = prof.copy()
+    fs = d.populations()[:, :, 0]  # post-collision f*, [9][W] at x = 0
+    e, _, opp = oracle.lattice()
+    f = np.zeros_like(fs)
+    for i in range(9):
+        for y in range(W):
+            sy = y - e[i, 1]
+            f[i, y] = fs[i, sy] if 0 <= sy < W else fs[opp[i], y]
+    local = np.zeros(W)
+    for y in range(W):
+        rho = f[:, y].sum()
+        j = f[:, y] @ e.astype(float)
+        A = oracle.strain_A(f[:, y], rho, j[0], j[1])
+        local[y] = A / oracle.solve_tau(A, n, xi, 0.51, 2.0)
+    ux = d.moments()[1][:, 0]
+    # Eq. nn3 with D from central differences: only D_xy = D_yx = (du/dy)/2 is nonzero
+    dudy = (ux[2:] - ux[:-2]) / 2.0
+    PiD = -0.25 * dudy ** 2
+    fd = np.zeros(W)
+    fd[1:-1] = 2 * np.sqrt(np.abs(PiD))
+    rows = slice(3, W // 2 - 3)  # one half, away from the wall rows and the centre line
+    rel = np.abs(local[rows] - fd[rows]) / fd[rows]
+    assert rel.max() < 0.015, rel
