@@ -586,7 +586,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.store == "f64" else "f32", "data": "synthetic",
                 "config": {"workload": workload_name(w),
                            "nodes": nodes, "fluid_nodes": fluid, "store": args.store,
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
