@@ -489,7 +489,9 @@ def main():
                 "kernel_share": kk / max(kf + kl + kk, 1e-9),
                 "particle_kernel_ms": kf / args.profile_steps,
                 "particle_side_ms": kl / args.profile_steps,
-                "step_overlap": "far stream-collide items run concurrently with the particle launches"}
+                "step_overlap": "far stream-collide items run concurrently with the particle launches",
+                # the whole step against the same bound: fluid-node updates per second x bytes per update
+                "step_frac": fluid * args.steps / (ms * 1e-3) * 2 * 9 * S / 1e9 / peak}
 
     # ---- end to end through the C ABI with host buffers ------------------------------------
     # Upload the initial state from pinned host memory, then every step: advance and read
@@ -593,6 +595,7 @@ def main():
                            "l2": "no flush; per-step footprint (2 arenas) exceeds the 129 MB L2",
                            "launch": {"kernel": k1_name, "block": launch[1], "stages": launch[2],
                                       "grid": launch[3], "graph_steps": 8}},
+                "fluid_node_mlups": value * fluid / nodes,
                 "clocks": clk, "gpu_launches": args.steps * kernels_per_step,
                 "roofline": roofline, "e2e": e2e, "variants": variants, "ensemble": ens, "channel": chan, "grains": grains, "combined": comb, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
