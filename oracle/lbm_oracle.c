@@ -34,6 +34,8 @@ struct or_domain {
     int32_t* owner;        /* rasterisation at t: 0 or particle index + 1 */
     int32_t* owner_prev;   /* rasterisation at t-1 */
     double* diag;          /* np * OR_DIAG_N */
+    double* zlink;         /* np * 6: link friction matrix Z of the step (see or_newton_euler) */
+    or_particle* bnd;      /* per particle: r_c(t) with the mid-step velocities of the exchange */
     int64_t step;
     int64_t overlap_count; /* nodes found inside two particles */
 };
@@ -237,19 +239,66 @@ void or_collide_node(const or_params* p, const double* f, double* out, uint32_t 
 
 /* ---- Eqs. (MP5), (MP6) and the position update of Sec. 3 ----
  * m_p = rho_p pi R^2 and I_p = m_p R^2 / 2 (disk); the fluid density in the
- * buoyancy term is rho0.  The position moves with the OLD velocity U(t). */
-void or_newton_euler(or_particle* q, double Fx, double Fy, double T, double gx, double gy, double rho0) {
-    if (q->fixed) return;
+ * buoyancy term is rho0.  The position moves with the OLD velocity U(t).
+ *
+ * Generalised velocity X = (U, V, Omega).  The force of Eq. (MP1) on a link
+ * splits into a part that does not depend on the particle's motion,
+ * -2 f'_k e_k, and a part linear in the boundary velocity,
+ * -(2 rho0 omega_k / c_s^2)(u_b . e_k) e_k with u_b . e_k = a_k . X,
+ * a_k = (e_kx, e_ky, (r_b - r_c) x e_k).  Summed over the links with the torque
+ * of Eq. (MP4) this is -Z X, Z = sum_k (2 rho0 omega_k / c_s^2) a_k a_k^T.
+ * The link exchange happens half-way through the step (the bounced population
+ * meets the boundary node r_b, half-way between the nodes, at t + dt/2), so
+ * u_b is taken at mid-step, X_mid = (X(t) + X(t+dt)) / 2, on both sides of the
+ * link (force here, Eqs. (MP7)-(MP8) in the stream).  Eqs. (MP5)-(MP6) then read
+ *   diag(m, m, I) (X(t+dt) - X(t)) = F + m (1 - rho0/rho_p) g - Z X_mid,
+ * F = the motion-independent link force plus the covered/uncovered and
+ * Eq. (MP2) forces (F[2] the torque), a 3x3 linear system for X(t+dt).
+ * Returns X_mid in xmid (the held velocity for a fixed particle). */
+void or_newton_euler(or_particle* q, const double* F, const double* Z, double gx, double gy,
+                     double rho0, double* xmid) {
+    const double X0[3] = {q->U, q->V, q->Omega};
+    if (q->fixed) {
+        for (int j = 0; j < 3; ++j) xmid[j] = X0[j];
+        return;
+    }
     const double pi = 3.14159265358979323846264338327950288;
     const double m = q->rho_p * pi * q->R * q->R;
     const double I = 0.5 * m * q->R * q->R;
-    const double U0 = q->U, V0 = q->V, O0 = q->Omega;
-    q->U = U0 + Fx / m + (q->rho_p - rho0) / q->rho_p * gx;
-    q->V = V0 + Fy / m + (q->rho_p - rho0) / q->rho_p * gy;
-    q->Omega = O0 + T / I;
-    q->x += U0;
-    q->y += V0;
-    q->theta += O0;
+    const double Mv[3] = {m, m, I};
+    /* Z as a full symmetric matrix from its upper triangle zxx zxy zxO zyy zyO zOO */
+    const double Zm[3][3] = {{Z[0], Z[1], Z[2]}, {Z[1], Z[3], Z[4]}, {Z[2], Z[4], Z[5]}};
+    const double buoy = (q->rho_p - rho0) / q->rho_p;
+    const double G[3] = {F[0] + m * buoy * gx, F[1] + m * buoy * gy, F[2]};
+    /* (M + Z/2) X1 = (M - Z/2) X0 + G, by Cramer's rule */
+    double A[3][3], b[3];
+    for (int r = 0; r < 3; ++r) {
+        b[r] = Mv[r] * X0[r] + G[r];
+        for (int c = 0; c < 3; ++c) {
+            A[r][c] = 0.5 * Zm[r][c] + (r == c ? Mv[r] : 0.0);
+            b[r] -= 0.5 * Zm[r][c] * X0[c];
+        }
+    }
+    const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1])
+                     - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0])
+                     + A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    double X1[3];
+    for (int j = 0; j < 3; ++j) {
+        double Aj[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) Aj[r][c] = c == j ? b[r] : A[r][c];
+        const double dj = Aj[0][0] * (Aj[1][1] * Aj[2][2] - Aj[1][2] * Aj[2][1])
+                        - Aj[0][1] * (Aj[1][0] * Aj[2][2] - Aj[1][2] * Aj[2][0])
+                        + Aj[0][2] * (Aj[1][0] * Aj[2][1] - Aj[1][1] * Aj[2][0]);
+        X1[j] = dj / det;
+    }
+    for (int j = 0; j < 3; ++j) xmid[j] = 0.5 * (X0[j] + X1[j]);
+    q->U = X1[0];
+    q->V = X1[1];
+    q->Omega = X1[2];
+    q->x += X0[0];
+    q->y += X0[1];
+    q->theta += X0[2];
 }
 
 /* ---- Eq. (MP2): repulsion on the node at a from the node at b ---- */
@@ -284,7 +333,7 @@ or_domain* or_create(const or_params* p) {
 void or_destroy(or_domain* d) {
     if (!d) return;
     free(d->solid); free(d->f); free(d->fn); free(d->part);
-    free(d->owner); free(d->owner_prev); free(d->diag);
+    free(d->owner); free(d->owner_prev); free(d->diag); free(d->zlink); free(d->bnd);
     free(d);
 }
 
@@ -371,6 +420,10 @@ int or_add_particles(or_domain* d, int n, const or_particle* p) {
     d->np += n;
     d->diag = (double*)realloc(d->diag, sizeof(double) * OR_DIAG_N * (size_t)d->np);
     memset(d->diag, 0, sizeof(double) * OR_DIAG_N * (size_t)d->np);
+    d->zlink = (double*)realloc(d->zlink, sizeof(double) * 6 * (size_t)d->np);
+    memset(d->zlink, 0, sizeof(double) * 6 * (size_t)d->np);
+    d->bnd = (or_particle*)realloc(d->bnd, sizeof(or_particle) * (size_t)d->np);
+    memcpy(d->bnd, d->part, sizeof(or_particle) * (size_t)d->np);
     rasterise(d);
     memcpy(d->owner_prev, d->owner, sizeof(int32_t) * d->n);
     return (int)d->overlap_count;
@@ -413,7 +466,9 @@ static void particle_forces(or_domain* d) {
     for (int p = 0; p < d->np; ++p) {
         const or_particle* q = &d->part[p];
         double* dg = &d->diag[p * OR_DIAG_N];
+        double* Z = &d->zlink[p * 6];
         memset(dg, 0, sizeof(double) * OR_DIAG_N);
+        memset(Z, 0, sizeof(double) * 6);
 
         /* Eq. (MP1): exterior link r_v -> r_v + e_k with r_v inside p. */
         for (int y = 0; y < P->ny; ++y)
@@ -426,17 +481,24 @@ static void particle_forces(or_domain* d) {
                     const int64_t kf = IDX(d, fx, fy);
                     if (d->solid[kf] || d->owner[kf] != 0) continue;
                     const double bx = x + 0.5 * EX[k], by = y + 0.5 * EY[k];
-                    double ubx, uby;
-                    boundary_velocity(d, q, bx, by, &ubx, &uby);
-                    const double ube = ubx * EX[k] + uby * EY[k];
                     const double fprime = d->f[OPP[k] * d->n + kf]; /* population along -e_k at r_v+e_k */
-                    const double s = -2.0 * (fprime + P->rho0 * WI[k] * ube / CS2);
+                    /* the part of Eq. (MP1) that does not depend on u_b */
+                    const double s = -2.0 * fprime;
                     const double Fx = s * EX[k], Fy = s * EY[k];
                     const double rx = min_image(bx - q->x, P->nx, P->periodic_x);
                     const double ry = min_image(by - q->y, P->ny, P->periodic_y);
                     dg[0] += Fx;
                     dg[1] += Fy;
                     dg[2] += rx * Fy - ry * Fx;
+                    /* the part linear in u_b: -c (a . X) a with a = (e_x, e_y, r x e) */
+                    const double c = 2.0 * P->rho0 * WI[k] / CS2;
+                    const double a[3] = {EX[k], EY[k], rx * EY[k] - ry * EX[k]};
+                    Z[0] += c * a[0] * a[0];
+                    Z[1] += c * a[0] * a[1];
+                    Z[2] += c * a[0] * a[2];
+                    Z[3] += c * a[1] * a[1];
+                    Z[4] += c * a[1] * a[2];
+                    Z[5] += c * a[2] * a[2];
                 }
             }
 
@@ -548,7 +610,8 @@ static void stream(or_domain* d) {
                 if (d->solid[t]) { d->fn[OPP[i] * n + k] = fi; continue; }
                 const int32_t ox = d->owner[k], ot = d->owner[t];
                 if (ox != ot && (ox == 0 || ot == 0)) {
-                    const or_particle* q = &d->part[(ox ? ox : ot) - 1];
+                    /* r_c(t) and the mid-step velocities (see or_newton_euler) */
+                    const or_particle* q = &d->bnd[(ox ? ox : ot) - 1];
                     double ubx, uby;
                     boundary_velocity(d, q, x + 0.5 * EX[i], y + 0.5 * EY[i], &ubx, &uby);
                     const double ube = ubx * EX[i] + uby * EY[i];
@@ -608,20 +671,36 @@ static void collide_all(or_domain* d) {
 
 void or_step(or_domain* d, int64_t nsteps) {
     for (int64_t s = 0; s < nsteps; ++s) {
-        /* 1. forces on the particles at t (MP1-MP4) */
-        if (d->np) particle_forces(d);
-        /* 2. stream with bounce-back (e.LB1 LHS, MP7, MP8) */
+        if (d->np) {
+            /* 1. forces on the particles at t (MP1-MP4) */
+            particle_forces(d);
+            /* 2. Newton-Euler (MP5, MP6) with the mid-step boundary velocity;
+             *    the link force reported is the full Eq. (MP1) at that velocity */
+            for (int p = 0; p < d->np; ++p) {
+                double* dg = &d->diag[p * OR_DIAG_N];
+                const double* Z = &d->zlink[p * 6];
+                const double F[3] = {dg[0] + dg[3] + dg[6], dg[1] + dg[4] + dg[7], dg[2] + dg[5] + dg[8]};
+                or_particle* q = &d->part[p];
+                d->bnd[p] = *q;
+                double xm[3];
+                or_newton_euler(q, F, Z, d->p.gx, d->p.gy, d->p.rho0, xm);
+                d->bnd[p].U = xm[0];
+                d->bnd[p].V = xm[1];
+                d->bnd[p].Omega = xm[2];
+                dg[0] -= Z[0] * xm[0] + Z[1] * xm[1] + Z[2] * xm[2];
+                dg[1] -= Z[1] * xm[0] + Z[3] * xm[1] + Z[4] * xm[2];
+                dg[2] -= Z[2] * xm[0] + Z[4] * xm[1] + Z[5] * xm[2];
+            }
+        }
+        /* 3. stream with bounce-back (e.LB1 LHS, MP7, MP8) */
         stream(d);
-        /* 3. open inlet / outlet columns */
+        /* 4. open inlet / outlet columns */
         if (d->p.inlet_outlet) inlet_outlet(d);
-        /* 4. collide at t+1 with noise (e.LB1 RHS, e.LB2, nn5, NP1) */
+        /* 5. collide at t+1 with noise (e.LB1 RHS, e.LB2, nn5, NP1) */
         collide_all(d);
-        /* 5. Newton-Euler (MP5, MP6), then re-rasterise */
+        /* 6. particles at their new positions: re-rasterise */
         if (d->np) {
             for (int p = 0; p < d->np; ++p) {
-                const double* dg = &d->diag[p * OR_DIAG_N];
-                or_newton_euler(&d->part[p], dg[0] + dg[3] + dg[6], dg[1] + dg[4] + dg[7],
-                                dg[2] + dg[5] + dg[8], d->p.gx, d->p.gy, d->p.rho0);
                 or_particle* q = &d->part[p];
                 if (d->p.periodic_x) q->x = q->x - d->p.nx * floor(q->x / d->p.nx);
                 if (d->p.periodic_y) q->y = q->y - d->p.ny * floor(q->y / d->p.ny);

@@ -20,10 +20,13 @@
  *
  * State convention: the stored populations are the POST-collision values
  * f*(x,t) (the populations about to stream).  One oracle step computes the
- * particle forces at t from f*(t), streams with bounce-back (t -> t+1),
- * applies the inlet/outlet columns, collides at t+1 (adding noise), moves the
- * particles and re-rasterises them.  Over n steps this is the paper's
- * collide-then-stream sequence shifted by half a step.
+ * particle forces at t from f*(t), advances the particle velocities (Eqs.
+ * MP5-MP6, with the boundary velocity of the link exchange taken at mid-step,
+ * see or_newton_euler), streams with bounce-back (t -> t+1) using that same
+ * mid-step boundary velocity in Eqs. MP7-MP8, applies the inlet/outlet
+ * columns, collides at t+1 (adding noise) and re-rasterises the particles at
+ * their new positions.  Over n steps this is the paper's collide-then-stream
+ * sequence shifted by half a step.
  *
  * Population layout of every array crossing this interface: f[q][y][x],
  * x fastest, q = 0..8 in the paper's order (Sec. 2): e0=(0,0), e1..e4 axis
@@ -93,8 +96,12 @@ void   or_collide_node(const or_params* p, const double* f9, double* out9,
 void   or_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out);
 void   or_thetas(uint64_t seed, uint32_t node, uint32_t step, uint32_t domain, double* theta6);
 void   or_noise(double rho, double kT, double omega, const double* theta6, double* zeta9);
-void   or_newton_euler(or_particle* p, double Fx, double Fy, double T,
-                       double gx, double gy, double rho0);
+/* Eqs. (MP5)-(MP6) with the mid-step boundary velocity: F = (Fx, Fy, T) the
+ * force and torque that do not depend on the particle's motion, Z[6] the upper
+ * triangle (xx xy xO yy yO OO) of the link friction matrix; returns the
+ * mid-step (U, V, Omega) in xmid[3]. */
+void   or_newton_euler(or_particle* p, const double* F, const double* Z,
+                       double gx, double gy, double rho0, double* xmid);
 void   or_lj_pair_force(double ax, double ay, double bx, double by,
                         double psi, double rit, double* F2);
 

@@ -106,7 +106,8 @@ def lib():
                 "or_philox4x32_10": (None, [_u32p, _u32p, _u32p]),
                 "or_thetas": (None, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _dp]),
                 "or_noise": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp]),
-                "or_newton_euler": (None, [_P(Particle)] + [ctypes.c_double] * 6),
+                "or_newton_euler": (None, [_P(Particle), _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, _dp]),
                 "or_lj_pair_force": (None, [ctypes.c_double] * 6 + [_dp]),
             }
             for name, (res, args) in sig.items():
@@ -293,10 +294,16 @@ def noise(rho, kT, omega, theta6):
     return out
 
 
-def newton_euler(particle: dict, Fx, Fy, T, gx, gy, rho0):
+def newton_euler(particle: dict, Fx, Fy, T, gx, gy, rho0, Z=(0.0,) * 6):
+    """One step of Eqs. MP5-MP6: returns (new particle dict, mid-step (U, V, Omega)).
+    Z = upper triangle (xx, xy, xO, yy, yO, OO) of the link friction matrix."""
     arr = particle_array([particle])
-    lib().or_newton_euler(arr, Fx, Fy, T, gx, gy, rho0)
-    return particle_dicts(arr, 1)[0]
+    F = np.array([Fx, Fy, T], dtype=np.float64)
+    Zv = np.ascontiguousarray(Z, dtype=np.float64)
+    xm = np.zeros(3)
+    lib().or_newton_euler(arr, _ptr(F, ctypes.c_double), _ptr(Zv, ctypes.c_double), gx, gy, rho0,
+                          _ptr(xm, ctypes.c_double))
+    return particle_dicts(arr, 1)[0], xm
 
 
 def lj_pair_force(a, b, psi, rit):

@@ -129,7 +129,8 @@ def test_moving_particle_momentum_ledger_and_mass(oracle):
 
 
 def test_newton_euler_closed_form(oracle):
-    """Constant F, T, g for n steps: U_n = U_0 + n a, x_n = x_0 + n U_0 + a n(n-1)/2."""
+    """Constant F, T, g for n steps with no link friction (Z = 0): U_n = U_0 + n a,
+    x_n = x_0 + n U_0 + a n(n-1)/2 (Eqs. MP5, MP6, position from the old U)."""
     q = dict(x=10.0, y=5.0, R=4.0, rho_p=1.5, U=0.01, V=-0.002, Omega=0.003, theta=0.1)
     Fx, Fy, T, gx, gy = 2e-3, -1e-3, 5e-4, 1e-6, 2e-6
     m = 1.5 * PI * 16.0
@@ -140,13 +141,72 @@ def test_newton_euler_closed_form(oracle):
     s = dict(q)
     n = 25
     for _ in range(n):
-        s = oracle.newton_euler(s, Fx, Fy, T, gx, gy, 1.0)
+        s, _ = oracle.newton_euler(s, Fx, Fy, T, gx, gy, 1.0)
     assert s["U"] == pytest.approx(q["U"] + n * ax, rel=1e-13)
     assert s["x"] == pytest.approx(q["x"] + n * q["U"] + ax * n * (n - 1) / 2, rel=1e-13)
     assert s["y"] == pytest.approx(q["y"] + n * q["V"] + ay * n * (n - 1) / 2, rel=1e-13)
     assert s["theta"] == pytest.approx(q["theta"] + n * q["Omega"] + al * n * (n - 1) / 2, rel=1e-13)
-    held = oracle.newton_euler(dict(q, fixed=1), Fx, Fy, T, gx, gy, 1.0)
+    held, xm = oracle.newton_euler(dict(q, fixed=1), Fx, Fy, T, gx, gy, 1.0, Z=(3.0, 0, 0, 3.0, 0, 50.0))
     assert held["x"] == q["x"] and held["U"] == q["U"]
+    assert list(xm) == [q["U"], q["V"], q["Omega"]]
+
+
+def test_newton_euler_mid_step_friction_closed_form(oracle):
+    """Link friction z along x alone, constant force F: with the boundary velocity at
+    mid-step, m (U1 - U0) = F - z (U0 + U1)/2, so U_n - F/z = r^n (U_0 - F/z) with
+    r = (m - z/2)/(m + z/2), and the mid-step velocity is (U0 + U1)/2."""
+    q = dict(x=3.0, y=4.0, R=5.0, rho_p=1.0, U=2e-3, V=0.0, Omega=0.0)
+    m = PI * 25.0
+    z, F = 22.7, 3e-4
+    r = (m - z / 2) / (m + z / 2)
+    s = dict(q)
+    for n in range(1, 40):
+        U0 = s["U"]
+        s, xm = oracle.newton_euler(s, F, 0.0, 0.0, 0.0, 0.0, 1.0, Z=(z, 0, 0, 0, 0, 0))
+        assert s["U"] == pytest.approx(F / z + r ** n * (q["U"] - F / z), rel=1e-12)
+        assert xm[0] == pytest.approx(0.5 * (U0 + s["U"]), rel=1e-15)
+        assert s["V"] == 0.0 and s["Omega"] == 0.0
+
+
+def test_newton_euler_mid_step_keeps_white_noise_equipartition(oracle):
+    """The fluctuation-dissipation balance of the link exchange: the fluid's
+    populations at equilibrium give the motion-independent link force a variance of
+    2 z kT per step (Var f_k = w_k rho0 kT / c_s^2 on each of the z = sum 2 rho0 w_k /
+    c_s^2 e_kx^2 links).  For the update U1 = r U0 + g F the stationary variance is
+    g^2 2 z kT / (1 - r^2); with the mid-step boundary velocity it is exactly kT / m
+    for any z (an explicit update, u_b at t, would give kT / (m - z/2))."""
+    m = PI * 25.0
+    for z in (1.0, 22.7, 60.0, 300.0):
+        base = dict(x=0.0, y=0.0, R=5.0, rho_p=1.0, U=0.0, V=0.0, Omega=0.0)
+        s1, _ = oracle.newton_euler(dict(base, U=1.0), 0.0, 0.0, 0.0, 0.0, 0.0, 1.0, Z=(z, 0, 0, 0, 0, 0))
+        s2, _ = oracle.newton_euler(dict(base), 1.0, 0.0, 0.0, 0.0, 0.0, 1.0, Z=(z, 0, 0, 0, 0, 0))
+        r, g = s1["U"], s2["U"]
+        kT = 1.0
+        var = g * g * 2.0 * z * kT / (1.0 - r * r)
+        assert var * m / kT == pytest.approx(1.0, rel=1e-12)
+
+
+def test_newton_euler_coupled_friction_solves_the_linear_system(oracle):
+    """Full 3x3 friction (translation-rotation coupling of an asymmetric link set):
+    (M + Z/2) X1 = (M - Z/2) X0 + F + m (1 - rho0/rho_p) g, checked against a
+    general linear solver (the oracle uses Cramer's rule)."""
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((3, 3))
+    Zm = B @ B.T * 5.0
+    Z = (Zm[0, 0], Zm[0, 1], Zm[0, 2], Zm[1, 1], Zm[1, 2], Zm[2, 2])
+    q = dict(x=1.0, y=2.0, R=6.0, rho_p=1.2, U=1e-3, V=-2e-3, Omega=3e-4)
+    m = 1.2 * PI * 36.0
+    Mm = np.diag([m, m, 0.5 * m * 36.0])
+    F = np.array([1e-3, -4e-4, 2e-3])
+    g = (2e-6, -1e-6)
+    X0 = np.array([q["U"], q["V"], q["Omega"]])
+    G = F + np.array([m * (0.2 / 1.2) * g[0], m * (0.2 / 1.2) * g[1], 0.0])
+    expect = np.linalg.solve(Mm + 0.5 * Zm, (Mm - 0.5 * Zm) @ X0 + G)
+    s, xm = oracle.newton_euler(q, *F, *g, 1.0, Z=Z)
+    got = np.array([s["U"], s["V"], s["Omega"]])
+    assert np.allclose(got, expect, rtol=1e-12, atol=0)
+    assert np.allclose(xm, 0.5 * (X0 + expect), rtol=1e-12, atol=0)
+    assert s["x"] == q["x"] + q["U"] and s["y"] == q["y"] + q["V"]
 
 
 def test_lj_pair_repulsive_and_power_13(oracle):
