@@ -408,37 +408,66 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
     __shared__ DiskF near_d[MAXNEAR];
     if (LO == 0 && role == 0) {
         // ------------------------------------------------------------------ role A
-        // Warps 0-3: the links, each with the force of Eq. MP1 and then the
-        // exchange of Eqs. MP7-MP8 on the same two slots (they belong to this
-        // link alone); warp 4: covered / uncovered nodes.  The Eq. MP2 force
-        // at t was summed by role D two steps earlier (or at set-up).
+        // The boundary velocity of the link exchange is the particle's
+        // velocity at mid-step, u_b = U_mid + Omega_mid x (r_b - r_c), on both
+        // sides of each link (Eq. MP1 and Eqs. MP7-MP8), so role A runs in three
+        // phases:
+        //  1. warps 0-3, over the links: the part of Eq. MP1 that does not
+        //     depend on u_b, -2 f'_k e_k (with its torque), and the sums that
+        //     give the link friction matrix Z = sum c_k a_k a_k^T,
+        //     c_k = 2 rho0 omega_k / c_s^2, a_k = (e_kx, e_ky, (r_b - r_c) x e_k);
+        //     warp 4: covered / uncovered nodes.  The Eq. MP2 force at t was
+        //     summed by role D two steps earlier (or at set-up).
+        //  2. thread 0: Eqs. MP5-MP6 with the force -Z X_mid of the moving
+        //     boundary, X_mid = (X(t) + X(t+1)) / 2: the SPD system
+        //     (M + Z/2) X_mid = M X(t) + G/2 by its adjugate, X(t+1) = 2 X_mid - X(t).
+        //  3. warps 0-3: the exchange of Eqs. MP7-MP8 with u_b(X_mid) on each
+        //     link's two slots (they belong to this link alone).
+        // FP64 issue is scarce on this part, so the per-link work is kept off
+        // it.  With r_c = (i + fx, j + fy), i, j integers, the arm of a link
+        // is r_b - r_c = (m_x - fx, m_y - fy) with m half-integers, and
+        // (r_b - r_c) x e_k = A/2 - B_k, A = 2 (m_x e_ky - m_y e_kx) an integer,
+        // B_k = fx e_ky - fy e_kx.  Every entry of Z is then a combination of
+        // integer sums over the links (weights W_k = c_k * 6 / rho0 = 4 on axis
+        // links, 1 on diagonal ones) with fx, fy applied once per particle, and
+        // the torque of the motion-independent force is -sum f' A + 2 fx S_y
+        // - 2 fy S_x with S = sum f' e_k: three FP64 additions per link.
         // Each warp sums its own terms by shuffles in a fixed order and the
         // warps are added in a fixed order, so the totals are deterministic.
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         __shared__ double wsa[A_BLOCK / 32][DIAG_N];  // per-warp partial sums
+        __shared__ int wsi[4][5];                     // per-warp integer sums Ixx, Ixy, Iyy, J1, J2
+        __shared__ long long wsk[4];                  // per-warp integer sum K
+        __shared__ double xmid[3];
         const int32_t* links = a.links + (int64_t)par * a.links_total;
         const int32_t* flips = a.flips + (int64_t)par * a.flips_total;
         const int nl = nl2[par], nf = nf2[par];
         // the Eq. MP2 sums of t, loaded now by the threads that add them up
         double ljc = 0.0;
-        if (threadIdx.x >= 6 && threadIdx.x < 9 && D.lj_psi != 0.0)
+        if (threadIdx.x >= 6 && threadIdx.x < 9 && D.lj_psi != 0.0 && D.lj_rit > 0.0)
             ljc = a.ljf[4 * ((int64_t)par * a.np + p) + (threadIdx.x - 6)];
         const bool forces = modes & PL_FORCES, swap = modes & PL_SWAP;
         double acc[DIAG_N];
 #pragma unroll
         for (int c = 0; c < DIAG_N; ++c) acc[c] = 0.0;
+        const A scl = (A)D.scale, inv = (A)D.inv_scale;
+        // integer node of the centre and the fractional offset
+        const double fl_x = floor(q.x), fl_y = floor(q.y);
+        const int ix = (int)fl_x, iy = (int)fl_y;
+        const double fxd = q.x - fl_x, fyd = q.y - fl_y;
+        // one round of four links per thread covers nl <= 512: the slot
+        // values then stay in registers from phase 1 to phase 3
+        const bool one_round = nl <= 4 * 128;
+        A va[4], vb[4];
         if (warp < 4) {
-            // Eq. MP1: F = -2 [f'_k(r_v + e_k, t*) + rho0 omega_k (u_b . e_k) / c_s^2] e_k
-            const A scl = (A)D.scale, inv = (A)D.inv_scale;
-            if (forces || swap) {
-                // four links per thread at a time: all eight slot loads are in
+            int Ixx = 0, Ixy = 0, Iyy = 0, J1 = 0, J2 = 0;
+            long long K = 0;
+            if (forces) {
+                // four links per thread at a time: the eight slot loads are in
                 // flight before any is used
 #pragma unroll 1
                 for (int l0 = threadIdx.x; l0 < nl; l0 += 4 * 128) {
-                    typename S::T* sa[4];
-                    typename S::T* sb[4];
-                    A va[4], vb[4];
-                    int kk[4], vxs[4], vys[4];
+                    int kk[4], a2s[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int l = l0 + 128 * u;
@@ -448,36 +477,30 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
                         int fx = vx + cx(k), fy = vy + cy(k);
                         wrap_node(D, fx, fy);
                         kk[u] = k;
-                        vxs[u] = vx;
-                        vys[u] = vy;
-                        sa[u] = base + (int64_t)k * D.plane + node;                          // pulled by r_v + e_k
-                        sb[u] = base + (int64_t)opp(k) * D.plane + (int64_t)fy * D.pitch + fx;  // pulled by r_v
+                        const int mx2 = 2 * wrap_off(vx - ix, D.nx, px) + cx(k);
+                        const int my2 = 2 * wrap_off(vy - iy, D.ny, py) + cy(k);
+                        a2s[u] = mx2 * cy(k) - my2 * cx(k);
                         if (l < nl) {
-                            va[u] = to_a(*sa[u], inv);
-                            vb[u] = to_a(*sb[u], inv);
+                            va[u] = to_a(base[(int64_t)k * D.plane + node], inv);
+                            vb[u] = to_a(base[(int64_t)opp(k) * D.plane + (int64_t)fy * D.pitch + fx], inv);
                         }
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         if (l0 + 128 * u >= nl) break;
-                        const int k = kk[u];
-                        const double bx = min_image((vxs[u] + 0.5 * cx(k)) - q.x, D.nx, px);
-                        const double by = min_image((vys[u] + 0.5 * cy(k)) - q.y, D.ny, py);
-                        const double ubx = q.U - q.Om * by, uby = q.V + q.Om * bx;
-                        const double ube = ubx * cx(k) + uby * cy(k);
-                        if (forces) {
-                            const double fo = S::SHIFT ? (double)vb[u] + wgt(opp(k)) * D.rho0 : (double)vb[u];
-                            const double sF = -2.0 * (fo + D.rho0 * wgt(k) * ube * 3.0);
-                            const double Fx = sF * cx(k), Fy = sF * cy(k);
-                            acc[0] += Fx;
-                            acc[1] += Fy;
-                            acc[2] += bx * Fy - by * Fx;
-                        }
-                        if (swap) {
-                            const A corr = (A)(2.0 * D.rho0 * wgt(k) * ube * 3.0);
-                            from_a(vb[u] + corr, scl, *sa[u]);
-                            from_a(va[u] - corr, scl, *sb[u]);
-                        }
+                        const int k = kk[u], ex = cx(k), ey = cy(k), a2 = a2s[u];
+                        // f'_{-k}(r_v + e_k), the population that r_v pulls across the link
+                        const double fo = S::SHIFT ? (double)vb[u] + wgt(opp(k)) * D.rho0 : (double)vb[u];
+                        if (ex) acc[0] += ex > 0 ? fo : -fo;
+                        if (ey) acc[1] += ey > 0 ? fo : -fo;
+                        acc[2] += fo * (double)a2;
+                        const int W = k <= 4 ? 4 : 1;
+                        Ixx += W * ex * ex;
+                        Ixy += W * ex * ey;
+                        Iyy += W * ey * ey;
+                        J1 += W * ex * a2;
+                        J2 += W * ey * a2;
+                        K += (long long)(W * a2) * a2;
                     }
                 }
             }
@@ -487,9 +510,25 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
                     const double x = warp_sum(acc[c]);
                     if (lane == 0) wsa[warp][c] = x;
                 }
+                const int r0 = __reduce_add_sync(0xffffffffu, Ixx), r1 = __reduce_add_sync(0xffffffffu, Ixy);
+                const int r2 = __reduce_add_sync(0xffffffffu, Iyy), r3 = __reduce_add_sync(0xffffffffu, J1);
+                const int r4 = __reduce_add_sync(0xffffffffu, J2);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) K += __shfl_down_sync(0xffffffffu, K, o);
+                if (lane == 0) {
+                    wsi[warp][0] = r0;
+                    wsi[warp][1] = r1;
+                    wsi[warp][2] = r2;
+                    wsi[warp][3] = r3;
+                    wsi[warp][4] = r4;
+                    wsk[warp] = K;
+                }
             } else if (lane == 0) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) wsa[warp][c] = 0.0;
+#pragma unroll
+                for (int c = 0; c < 5; ++c) wsi[warp][c] = 0;
+                wsk[warp] = 0;
             }
         } else if (warp == 4) {
             // Covered (+) / uncovered (-) nodes: F = +- rho (u - U_p), with rho and
@@ -523,28 +562,67 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
             }
         }
         __syncthreads();
+        __shared__ long long itot[6];
         if (forces && threadIdx.x < DIAG_N) {
-            // component groups: links 0-2 (warps 0-3), covered/uncovered 3-5 and
-            // 9-12 (warp 4), LJ 6-8 (role D, earlier launch); fixed order
+            // component groups: link sums 0-2 (warps 0-3), covered/uncovered 3-5
+            // and 9-12 (warp 4), LJ 6-8 (role D, earlier launch); fixed order
             const int c = threadIdx.x;
             double x = 0.0;
             if (c < 3) x = ((wsa[0][c] + wsa[1][c]) + wsa[2][c]) + wsa[3][c];
             else if (c < 6 || c >= 9) x = wsa[4][c];
             else x = ljc;
             tot[c] = x;
-            a.diag[(int64_t)p * DIAG_N + c] = x;
+            if (c >= 3) a.diag[(int64_t)p * DIAG_N + c] = x;
+        } else if (forces && threadIdx.x >= 32 && threadIdx.x < 38) {
+            const int c = threadIdx.x - 32;
+            itot[c] = c < 5 ? (long long)wsi[0][c] + wsi[1][c] + wsi[2][c] + wsi[3][c]
+                            : wsk[0] + wsk[1] + wsk[2] + wsk[3];
         }
         __syncthreads();
-        if (advance && threadIdx.x == 0) {
-            // Eqs. MP5, MP6 (velocities) with r_c(t+1) = r_c(t) + U_p(t).
+        __shared__ double zsh[6], f0sh[3];
+        if (threadIdx.x == 0) {
+            // Eqs. MP5, MP6 (velocities) with r_c(t+1) = r_c(t) + U_p(t).  One
+            // thread, FP64: the dependent chain is kept short (one reciprocal).
             PartState n = q;
-            if (!st.fixed) {
+            double xm[3] = {q.U, q.V, q.Om};
+            double F0x = 0.0, F0y = 0.0, T0 = 0.0, z[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            if (forces) {
+                // the motion-independent link force and torque
+                F0x = -2.0 * tot[0];
+                F0y = -2.0 * tot[1];
+                T0 = -tot[2] + 2.0 * fxd * tot[1] - 2.0 * fyd * tot[0];
+                // Z = rho0/6 x (integer sums with the fractional offset applied)
+                const double Ixx = (double)itot[0], Ixy = (double)itot[1], Iyy = (double)itot[2];
+                const double J1 = (double)itot[3], J2 = (double)itot[4], Kd = (double)itot[5];
+                const double r6 = D.rho0 / 6.0;
+                z[0] = r6 * Ixx;
+                z[1] = r6 * Ixy;
+                z[2] = r6 * (0.5 * J1 - fxd * Ixy + fyd * Ixx);
+                z[3] = r6 * Iyy;
+                z[4] = r6 * (0.5 * J2 - fxd * Iyy + fyd * Ixy);
+                z[5] = r6 * (0.25 * Kd - (fxd * J2 - fyd * J1) + fxd * fxd * Iyy - 2.0 * fxd * fyd * Ixy +
+                             fyd * fyd * Ixx);
+            }
+            if (advance && !st.fixed) {
                 if (forces) {
-                    const double Fx = (tot[0] + tot[3]) + tot[6], Fy = (tot[1] + tot[4]) + tot[7];
-                    const double T = (tot[2] + tot[5]) + tot[8];
-                    n.U = q.U + Fx * st.inv_m + st.buoy * D.gx;
-                    n.V = q.V + Fy * st.inv_m + st.buoy * D.gy;
-                    n.Om = q.Om + T * st.inv_I;
+                    // G = motion-independent force and torque + buoyancy term
+                    const double G0 = (F0x + tot[3]) + tot[6] + st.m * st.buoy * D.gx;
+                    const double G1 = (F0y + tot[4]) + tot[7] + st.m * st.buoy * D.gy;
+                    const double G2 = (T0 + tot[5]) + tot[8];
+                    // (M + Z/2) X_mid = M X(t) + G/2, M + Z/2 symmetric positive
+                    // definite: X_mid = adj(M + Z/2) r / det(M + Z/2)
+                    const double a00 = st.m + 0.5 * z[0], a01 = 0.5 * z[1], a02 = 0.5 * z[2];
+                    const double a11 = st.m + 0.5 * z[3], a12 = 0.5 * z[4], a22 = st.I + 0.5 * z[5];
+                    const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+                    const double c11 = a00 * a22 - a02 * a02, c12 = a01 * a02 - a00 * a12, c22 = a00 * a11 - a01 * a01;
+                    const double inv_det = 1.0 / (a00 * c00 + a01 * c01 + a02 * c02);
+                    const double r0 = st.m * q.U + 0.5 * G0, r1 = st.m * q.V + 0.5 * G1, r2 = st.I * q.Om + 0.5 * G2;
+                    xm[0] = (c00 * r0 + c01 * r1 + c02 * r2) * inv_det;
+                    xm[1] = (c01 * r0 + c11 * r1 + c12 * r2) * inv_det;
+                    xm[2] = (c02 * r0 + c12 * r1 + c22 * r2) * inv_det;
+                    n.U = 2.0 * xm[0] - q.U;
+                    n.V = 2.0 * xm[1] - q.V;
+                    n.Om = 2.0 * xm[2] - q.Om;
                 }
                 next_position(D, q, false, n.x, n.y);
                 n.th = q.th + q.Om;
@@ -558,9 +636,63 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
                     atomicOr(a.err, ERR_STATE);
                     n = q;
                     n.U = n.V = n.Om = 0.0;
+                    xm[0] = xm[1] = xm[2] = 0.0;
                 }
             }
-            a.state[(int64_t)(par ^ 1) * a.np + p] = n;
+            if (advance) a.state[(int64_t)(par ^ 1) * a.np + p] = n;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) zsh[c] = z[c];
+            f0sh[0] = F0x;
+            f0sh[1] = F0y;
+            f0sh[2] = T0;
+            xmid[0] = xm[0];
+            xmid[1] = xm[1];
+            xmid[2] = xm[2];
+        }
+        __syncthreads();
+        if (forces && warp == 4 && lane < 3) {
+            // the link force of Eq. MP1 at the mid-step boundary velocity, beside the exchange
+            const int c = lane;
+            const int i0 = c == 0 ? 0 : (c == 1 ? 1 : 2), i1 = c == 0 ? 1 : (c == 1 ? 3 : 4),
+                      i2 = c == 0 ? 2 : (c == 1 ? 4 : 5);
+            a.diag[(int64_t)p * DIAG_N + c] = f0sh[c] - (zsh[i0] * xmid[0] + zsh[i1] * xmid[1] + zsh[i2] * xmid[2]);
+        }
+        if (swap && warp < 4) {
+            // Eqs. MP7-MP8 as a pre-stream exchange with u_b at mid-step:
+            // u_b . e_k = U e_kx + V e_ky + Omega (A/2 - B_k), in the store's
+            // arithmetic type
+            const A Um = (A)xmid[0], Vm = (A)xmid[1], Om = (A)xmid[2];
+            const A fxa = (A)fxd, fya = (A)fyd, r6a = (A)(6.0 * D.rho0);
+#pragma unroll 1
+            for (int l0 = threadIdx.x; l0 < nl; l0 += 4 * 128) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int l = l0 + 128 * u;
+                    if (l >= nl) break;
+                    const int32_t e = links[st.link_off + l];
+                    const int node = e >> 3, k = (e & 7) + 1;
+                    const int vy = node / D.pitch, vx = node - vy * D.pitch;
+                    int fx = vx + cx(k), fy = vy + cy(k);
+                    wrap_node(D, fx, fy);
+                    typename S::T* sa = base + (int64_t)k * D.plane + node;                          // pulled by r_v + e_k
+                    typename S::T* sb = base + (int64_t)opp(k) * D.plane + (int64_t)fy * D.pitch + fx;  // pulled by r_v
+                    A xa, xb;
+                    if (one_round && forces) {
+                        xa = va[u];
+                        xb = vb[u];
+                    } else {
+                        xa = to_a(*sa, inv);
+                        xb = to_a(*sb, inv);
+                    }
+                    const int mx2 = 2 * wrap_off(vx - ix, D.nx, px) + cx(k);
+                    const int my2 = 2 * wrap_off(vy - iy, D.ny, py) + cy(k);
+                    const A arm = (A)0.5 * (A)(mx2 * cy(k) - my2 * cx(k)) - (fxa * (A)cy(k) - fya * (A)cx(k));
+                    const A ube = Um * (A)cx(k) + Vm * (A)cy(k) + Om * arm;
+                    const A corr = r6a * (A)wgt(k) * ube;
+                    from_a(xb + corr, scl, *sa);
+                    from_a(xa - corr, scl, *sb);
+                }
+            }
         }
         return;
     }
@@ -596,7 +728,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
         // runs off the path of the force and exchange launches.  Warps 5-7
         // prepare (their own named barrier), then all eight warps take the
         // surface nodes; fixed-order sums into ljf[(t+1) & 1].
-        if (!(D.lj_psi != 0.0)) return;
+        if (!(D.lj_psi != 0.0 && D.lj_rit > 0.0)) return;  // no pair within a zero threshold
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const DiskF kd = uni.kn;  // the disk at the target step
         const Box bd = uni.bn;
@@ -604,6 +736,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
         double acc[DIAG_N];
 #pragma unroll
         for (int c = 0; c < DIAG_N; ++c) acc[c] = 0.0;
+        int wall_near = 0;
         if (warp >= LJ_W0) {
             // Set-up: the other particles within reach, the pair-force
             // table, the inside bitmap of this disk and those of nearby disks.
@@ -637,6 +770,37 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
                     if (gt == 0) nnear += tot_hit;
                     lj_sync();
                 }
+            }
+        } else {
+            // Warps 0-4 meanwhile look at the wall / solid field over the box
+            // of the disk: any nonzero value (or a box node beyond an open end,
+            // summed on the spot below) means the wall term may not vanish.
+            const Box b = bd;
+#pragma unroll 1
+            for (int i = threadIdx.x; i < b.n(); i += LJ_W0 * 32) {
+                const int yr = i / b.w;
+                int ax = b.x0 + (i - yr * b.w), ay = b.y0 + yr;
+                if (!wrap_node(D, ax, ay)) {
+                    if ((ax < 0 || ax >= D.nx) && !(D.flags & FLAG_PX)) wall_near = 1;
+                    continue;
+                }
+                const double2 fw = a.ljwall[D.node_off + (int64_t)ay * D.pitch + ax];
+                if (fw.x != 0.0 || fw.y != 0.0) wall_near = 1;
+            }
+        }
+        // An isolated particle -- no other particle within reach, no nonzero
+        // wall field around it -- feels no Eq. MP2 force: its sums are exactly
+        // zero, so the surface list and the pair loops are skipped.
+        if (!__syncthreads_or(wall_near) && nnear == 0) {
+            if (threadIdx.x >= 6 && threadIdx.x < 9) {
+                const int64_t tn = advance ? t + 1 : t;
+                a.ljf[4 * ((int64_t)(tn & 1) * a.np + p) + (threadIdx.x - 6)] = 0.0;
+            }
+            return;
+        }
+        if (warp >= LJ_W0) {
+            const int gt = (int)threadIdx.x - LJ_W0 * 32;
+            {
                 const int nn = nnear < MAXNEAR ? nnear : MAXNEAR;
                 const Box b = bd;
                 const Box e = {b.x0 - 1, b.y0 - 1, b.w + 2, b.h + 2};

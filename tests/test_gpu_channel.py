@@ -12,9 +12,8 @@ radius 7.5, kT = 5e-5, nu = 0.1, no external force).
   near kT, its velocity autocorrelation dies out, and its mean-squared
   displacement along the channel crosses over from ballistic (local exponent
   near 2) to diffusive (near 1), the behaviour the paper recalls for this
-  benchmark.  The exact values are set by the particle coupling, which the paper
-  leaves open (exterior links plus covered / uncovered nodes here), so the
-  bounds are the statistical ones of a run of this length.
+  benchmark.  A single disk over 60,000 steps gives intervals of a few
+  percent; the 2 % statement is tested on many disks (test_gpu_brownian.py).
 """
 import math
 
@@ -54,7 +53,9 @@ def test_confined_channel_parity(store, steps, lim, errlog):
     ref.step(steps)
     ctx.step(steps)
     fr, fg = ref.populations(), ctx.populations()
-    err = float(np.abs(fg - fr).max() / np.abs(fr).max())
+    # largest difference over the largest shifted population |f - omega_i rho0|
+    w9 = oracle.feq(1.0, 0.0, 0.0)[:, None, None]
+    err = float(np.abs(fg - fr).max() / np.abs(fr - w9).max())
     pr, pg = ref.particles()[0], ctx.particles()[0]
     perr = max(abs(pr[k] - pg[k]) for k in ("x", "y", "U", "V", "Omega"))
     errlog(store=store, steps=steps, pointwise=err, particle=perr)
@@ -91,6 +92,12 @@ def test_confined_channel_thermalisation_and_brownian_disk(errlog):
     ctx.sync()  # no device error over the run
     T = (U[:, :2] ** 2).mean(axis=0) * M / kT
     T_rot = (U[:, 2] ** 2).mean() * (0.5 * M * q["R"] ** 2) / kT
+    # 95 % intervals from block means of 3,000 steps (about 30 velocity
+    # correlation times of this disk, so the blocks are nearly independent)
+    blk = 3000
+    bm = (U[: n // blk * blk] ** 2).reshape(n // blk, blk, 3).mean(axis=1)
+    bm *= np.array([M, M, 0.5 * M * q["R"] ** 2]) / kT
+    ci = 1.96 * bm.std(axis=0, ddof=1) / math.sqrt(bm.shape[0])
 
     def acf(v, nl):
         f = np.fft.rfft(v, 2 * len(v))
@@ -101,11 +108,14 @@ def test_confined_channel_thermalisation_and_brownian_disk(errlog):
     msd = {lag: float(((xs[lag:] - xs[:-lag]) ** 2).mean()) for lag in (1, 10, 1000, 10000)}
     exp_short = math.log(msd[10] / msd[1]) / math.log(10)
     exp_long = math.log(msd[10000] / msd[1000]) / math.log(10)
-    errlog(rows_x=rows[0].tolist(), rows_y=rows[1].tolist(), T=T.tolist(), T_rot=T_rot,
+    errlog(rows_x=rows[0].tolist(), rows_y=rows[1].tolist(), T=T.tolist(), T_rot=T_rot, ci=ci.tolist(),
            vacf_1000=float(C[1000] / C[0]), msd_exponent_1_10=exp_short, msd_exponent_1000_10000=exp_long)
     # each row: 40 snapshots of ~2,900 nodes; per-row standard error well under 1 %
     assert np.abs(rows - 1).max() < 0.03, rows
-    assert np.all((T > 0.85) & (T < 1.25)), T
-    assert 0.8 < T_rot < 1.3, T_rot
+    # one disk between walls (no momentum conservation, so no box factor): its
+    # kinetic temperatures must contain 1 in their 99 % intervals
+    Ts = np.array([T[0], T[1], T_rot])
+    assert np.all(np.abs(Ts - 1.0) < 2.58 / 1.96 * ci + 0.005), (Ts, ci)
+    assert np.all(ci < 0.08), ci
     assert abs(C[1000] / C[0]) < 0.1
     assert exp_short > 1.7 and exp_long < 1.25, (exp_short, exp_long)
