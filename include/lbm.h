@@ -122,7 +122,11 @@ int lbm_set_geometry(lbm_ctx* ctx, int dom, const uint8_t* solid);
 int lbm_add_particles(lbm_ctx* ctx, int dom, int n, const lbm_particle* p);
 
 /* Replace the populations f*(t) of domain dom with host FP64 values
- * f[9][ny][nx] (converted to the store type; solid nodes ignored). */
+ * f[9][ny][nx] (converted to the store type; solid nodes ignored).  It first
+ * waits for the queued steps and clears the context's sticky device error
+ * word (LBM_E_UNSTABLE, LBM_E_TIMEOUT, LBM_E_STATE of earlier steps, for every
+ * domain): the caller starts again from a known state.  Call lbm_sync before
+ * it to see such an error. */
 int lbm_set_populations(lbm_ctx* ctx, int dom, const double* f);
 
 /* Read the populations f*(t) of domain dom into host FP64 f[9][ny][nx]
@@ -175,13 +179,17 @@ int lbm_checks(lbm_ctx* ctx, int dom, double* out3);
 int64_t lbm_step_count(const lbm_ctx* ctx);
 
 /* Checkpoint: populations, particle state, rasterisation and step counter.
- * Because the noise is counter-based, a resumed run is bit-identical. */
+ * Because the noise is counter-based, a resumed run is bit-identical.
+ * lbm_load replaces the whole state and, like lbm_set_populations, clears the
+ * sticky device error word of earlier steps. */
 int lbm_save(lbm_ctx* ctx, const char* path);
 int lbm_load(lbm_ctx* ctx, const char* path);
 
 /* Pick the stream-and-collide kernel and launch shape (kernel, threads per
  * block and stages as in lbm_set_launch) by short timed trials on the
- * context's own data.  The trials write only the second population arena,
+ * context's own data, among the register-kernel grids 0, 1, 3 and 4 (kernel 3
+ * only without particles; the staged kernel 2 is chosen only through
+ * lbm_set_launch).  The trials write only the second population arena,
  * which the next step overwrites, so the state and step count are unchanged. */
 int lbm_autotune(lbm_ctx* ctx, int trial_steps);
 
@@ -200,6 +208,27 @@ int lbm_autotune(lbm_ctx* ctx, int trial_steps);
  * stages, grid} to out4. */
 int lbm_set_launch(lbm_ctx* ctx, int32_t kernel, int32_t block, int32_t stages);
 int lbm_get_launch(const lbm_ctx* ctx, int64_t* out4);
+
+/* Failure detection (no paper counterpart).  Every wait inside a kernel of
+ * this library is bounded: the staged stream-and-collide kernel (kernel 2 of
+ * lbm_set_launch) waits for its bulk copies at most `ns` nanoseconds of the
+ * GPU's global timer per stage (default 1e9), then records LBM_E_TIMEOUT,
+ * waits for its copies still in flight (always with the full second, so no
+ * copy lands in shared memory it has left) and ends its work; the next
+ * blocking call returns LBM_E_TIMEOUT and the populations of that step are
+ * not valid (reload them with lbm_set_populations or lbm_load).  ns = 0 makes
+ * every stage wait report expiry at once without waiting, which is how the
+ * tests exercise this path.  Takes effect from the next lbm_step.
+ * LBM_E_INVAL for ns above 60 s. */
+int lbm_set_wait_limit(lbm_ctx* ctx, uint64_t ns);
+
+/* Failure injection on the host (no paper counterpart): the nth device
+ * allocation that the library makes from now on (any context; creation,
+ * particles, staging buffers) fails as it would on an exhausted device, so
+ * that the caller sees LBM_E_NOMEM and the library frees whatever it had
+ * allocated for that call.  nth = 0 switches the hook off; it also goes off
+ * by itself once it has fired.  LBM_E_INVAL for nth < 0. */
+int lbm_debug_fail_alloc(int32_t nth);
 
 /* Measurement: advance nsteps timesteps with plain launches in sequence (no
  * graph, no overlap), enqueued back to back in batches of 32 steps with a
@@ -251,6 +280,9 @@ int lbm_fp64_fma_rate(void* cuda_stream, double* gflops_out);
  * Scratch is one static device array of LBM_NOALLOC_MAX_ROWS x 3 doubles
  * (384 KiB on every GPU that loads the library, until exit); ny above that
  * maximum is rejected with LBM_E_INVAL, as are bad sizes and a NULL buffer.
+ * A CUDA error already pending when the call starts is returned as
+ * LBM_E_CUDA and left pending; lbm_last_error(NULL) gives the reason of every
+ * LBM_E_INVAL and LBM_E_CUDA.
  * The first call on a device looks up the array's device address (the runtime
  * loads the module if it has not yet), so make that first call before any
  * stream capture.  All calls share the array: calls whose kernels may overlap

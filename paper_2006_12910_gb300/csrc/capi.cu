@@ -3,13 +3,15 @@
 // The context owns every device buffer: two population arenas (the state
 // f*(t) and the next state), per-node solid bytes, the per-chunk slow-path
 // bitmask, the step counters, a sticky error word and the particle arrays.
-// lbm_step replays a CUDA graph of GRAPH_STEPS timesteps; a timestep is
+// lbm_step replays CUDA graphs of GRAPH_STEPS timesteps (and one graph of
+// the remaining 1 .. GRAPH_STEPS-1 steps); a timestep is
 //   [particle forces + Newton-Euler] -> [link exchange + re-rasterise]
 //   -> [fused pull-stream + collide over every domain]
 // where the two particle kernels are skipped when no domain holds particles.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -25,6 +27,23 @@ namespace {
 
 constexpr int GRAPH_STEPS = 8;  // even, so a replay returns to the same arena
 thread_local std::string g_create_error = "no error";
+
+// Test hook of lbm_debug_fail_alloc: when positive, the device allocation
+// that brings it to zero fails as an exhausted device would.
+std::atomic<int> g_fail_alloc{0};
+
+// Every device allocation of the library goes through here.
+template <class T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+    int n = g_fail_alloc.load();
+    while (n > 0 && !g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
 
 size_t elem_bytes(int kind) { return kind == 0 ? 8 : (kind <= 2 ? 4 : 2); }
 
@@ -96,8 +115,12 @@ struct lbm_ctx {
     cudaEvent_t ev_pstate = nullptr;
     bool pstate_evt = false;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // GRAPH_STEPS steps from state 0 / 1
-    cudaGraphExec_t gexec1[2] = {nullptr, nullptr};  // one step from state 0 / 1
+    // gexecr[k][r]: r = 1 .. GRAPH_STEPS-1 steps from state k, so that any
+    // lbm_step(n) runs as whole multi-step graphs (the cross-step overlap of
+    // the particle and stream-collide chains holds inside every graph)
+    cudaGraphExec_t gexecr[2][GRAPH_STEPS] = {};
     bool graph_dirty = true;
+    uint64_t wait_ns = 1000000000ull;  // limit of the bounded device waits (lbm_set_wait_limit)
 
     int cur = 0;
     int64_t steps = 0;
@@ -246,7 +269,8 @@ void fill_dom(DomDev& D, const lbm_params& p, int kind) {
 // (1..8) marks a fluid node whose neighbour x + e_j is solid or lies in a
 // ghost row beyond a y wall (x wrapped when periodic; beyond an open end
 // there is no neighbour); the node writes its f*_j into that neighbour's slot
-// opp(j) after each collision.  Open columns carry the Zou-He bits, except on
+// opp(j) after each collision.  On a solid node bit i marks its slot i as such
+// a mailbox (the node x + e_i is fluid); its other slots are read by nobody.  Open columns carry the Zou-He bits, except on
 // wall rows, whose end nodes carry NF_CORNER (their sources beyond the x
 // range reflect from the node's own opposite slot); solid nodes NF_SOLID.  A
 // chunk bit is set when any of its nodes has a nonzero flag word.
@@ -261,7 +285,21 @@ void build_flags(const DomDev& D, const uint8_t* solid, std::vector<uint16_t>& f
             uint16_t f = 0;
             const bool wall_row = wy && (y == 0 || y == D.ny - 1);
             if (solid[(size_t)y * D.nx + x]) {
+                // bit i of a solid node: slot i is a mailbox, i.e. the node
+                // x + e_i exists (wrapped when periodic) and is fluid, and writes it
                 f = NF_SOLID;
+                for (int i = 1; i < 9; ++i) {
+                    int tx = x + ex[i], ty = y + ey[i];
+                    if (ty < 0 || ty >= D.ny) {
+                        if (wy) continue;
+                        ty = (ty + D.ny) % D.ny;
+                    }
+                    if (tx < 0 || tx >= D.nx) {
+                        if (!px) continue;
+                        tx = (tx + D.nx) % D.nx;
+                    }
+                    if (!solid[(size_t)ty * D.nx + tx]) f |= (uint16_t)(1u << i);
+                }
             } else {
                 for (int j = 1; j < 9; ++j) {
                     int tx = x + ex[j], ty = y + ey[j];
@@ -384,6 +422,7 @@ cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int bloc
     a.ctr_in = c->ctr + cur;
     a.ctr_out = c->ctr + (cur ^ 1);
     a.err = c->err;
+    a.wait_ns = c->wait_ns;
     a.mode = mode;
     a.flips = with_flips && c->np_active > 0 && mode != STREAM_FAR;
     a.mark = c->mark;
@@ -490,7 +529,7 @@ int capture_steps(lbm_ctx* c, int k, int nsteps, cudaGraphExec_t* out) {
 int build_graphs(lbm_ctx* c) {
     for (int k = 0; k < 2; ++k) {
         int r = capture_steps(c, k, GRAPH_STEPS, &c->gexec[k]);
-        if (!r) r = capture_steps(c, k, 1, &c->gexec1[k]);
+        for (int n = 1; n < GRAPH_STEPS && !r; ++n) r = capture_steps(c, k, n, &c->gexecr[k][n]);
         if (r) return r;
     }
     c->graph_dirty = false;
@@ -538,7 +577,7 @@ int ensure_stage(lbm_ctx* c, size_t bytes) {
     if (c->d_stage) cudaFree(c->d_stage);
     c->d_stage = nullptr;
     c->d_stage_bytes = 0;
-    CKC(c, cudaMalloc(&c->d_stage, bytes));
+    CKC(c, dev_malloc(&c->d_stage, bytes));
     c->d_stage_bytes = bytes;
     return LBM_OK;
 }
@@ -670,12 +709,12 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
         CKCR(cudaEventCreateWithFlags(&c->ev_rast[k], cudaEventDisableTiming));
         CKCR(cudaEventCreateWithFlags(&c->ev_lj[k], cudaEventDisableTiming));
     }
-    CKCR(cudaMalloc(&c->mark, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items)));
-    CKCR(cudaMalloc(&c->near_list, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items)));
-    CKCR(cudaMalloc(&c->near_cnt, sizeof(int32_t) * 3));
+    CKCR(dev_malloc(&c->mark, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items)));
+    CKCR(dev_malloc(&c->near_list, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items)));
+    CKCR(dev_malloc(&c->near_cnt, sizeof(int32_t) * 3));
     CKCR(cudaMemsetAsync(c->mark, 0xff, sizeof(int32_t) * 3 * std::max<int64_t>(1, c->total_items), c->stream));
     CKCR(cudaMemsetAsync(c->near_cnt, 0, sizeof(int32_t) * 3, c->stream));
-    CKCR(cudaMalloc(&c->fliptag, sizeof(int64_t) * 2 * std::max<size_t>(1, c->node_bytes)));
+    CKCR(dev_malloc(&c->fliptag, sizeof(int64_t) * 2 * std::max<size_t>(1, c->node_bytes)));
     CKCR(cudaMemsetAsync(c->fliptag, 0xff, sizeof(int64_t) * 2 * std::max<size_t>(1, c->node_bytes), c->stream));
     {
         // Eq. MP2 pair force per node offset within r_it, one table per domain
@@ -697,8 +736,8 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
                 }
             cnt[d] = m;
         }
-        CKCR(cudaMalloc(&c->lj_tab, sizeof(LjEntry) * tab.size()));
-        CKCR(cudaMalloc(&c->lj_cnt, sizeof(int32_t) * ndom));
+        CKCR(dev_malloc(&c->lj_tab, sizeof(LjEntry) * tab.size()));
+        CKCR(dev_malloc(&c->lj_cnt, sizeof(int32_t) * ndom));
         CKCR(cudaMemcpyAsync(c->lj_tab, tab.data(), sizeof(LjEntry) * tab.size(), cudaMemcpyHostToDevice, c->stream));
         CKCR(cudaMemcpyAsync(c->lj_cnt, cnt.data(), sizeof(int32_t) * ndom, cudaMemcpyHostToDevice, c->stream));
         CKCR(cudaStreamSynchronize(c->stream));
@@ -706,27 +745,27 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
     CKCR(cudaEventCreateWithFlags(&c->ev_snap, cudaEventDisableTiming));
     CKCR(cudaEventCreateWithFlags(&c->ev_pstate, cudaEventDisableTiming));
     CKCR(cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming));
-    CKCR(cudaMalloc(&c->f[0], c->arena_elems * c->esz));
-    CKCR(cudaMalloc(&c->f[1], c->arena_elems * c->esz));
-    CKCR(cudaMalloc(&c->solid, c->node_bytes));
-    CKCR(cudaMalloc(&c->nflags, c->node_bytes * 2));
-    CKCR(cudaMalloc(&c->special, std::max<size_t>(1, c->special_words) * 4));
+    CKCR(dev_malloc(&c->f[0], c->arena_elems * c->esz));
+    CKCR(dev_malloc(&c->f[1], c->arena_elems * c->esz));
+    CKCR(dev_malloc(&c->solid, c->node_bytes));
+    CKCR(dev_malloc(&c->nflags, c->node_bytes * 2));
+    CKCR(dev_malloc(&c->special, std::max<size_t>(1, c->special_words) * 4));
     {
         bool any_lj = false;
         for (int d = 0; d < ndom; ++d) any_lj |= per_domain[d].lj_psi > 0.0 && per_domain[d].lj_rit > 0.0;
         if (any_lj) {
-            CKCR(cudaMalloc(&c->ljwall, sizeof(double2) * std::max<size_t>(1, c->node_bytes)));
+            CKCR(dev_malloc(&c->ljwall, sizeof(double2) * std::max<size_t>(1, c->node_bytes)));
             CKCR(cudaMemsetAsync(c->ljwall, 0, sizeof(double2) * std::max<size_t>(1, c->node_bytes), c->stream));
         }
     }
-    CKCR(cudaMalloc(&c->dd, sizeof(DomDev) * ndom));
-    CKCR(cudaMalloc(&c->d_item_off, sizeof(int64_t) * ndom));
-    CKCR(cudaMalloc(&c->ctr, sizeof(int64_t) * 2));
-    CKCR(cudaMalloc(&c->pstep, sizeof(int64_t) * 2));
+    CKCR(dev_malloc(&c->dd, sizeof(DomDev) * ndom));
+    CKCR(dev_malloc(&c->d_item_off, sizeof(int64_t) * ndom));
+    CKCR(dev_malloc(&c->ctr, sizeof(int64_t) * 2));
+    CKCR(dev_malloc(&c->pstep, sizeof(int64_t) * 2));
     CKCR(cudaMemsetAsync(c->pstep, 0, sizeof(int64_t) * 2, c->stream));
-    CKCR(cudaMalloc(&c->err, sizeof(unsigned)));
-    CKCR(cudaMalloc(&c->d_partial, sizeof(double) * 3 * CHECK_BLOCKS));
-    CKCR(cudaMalloc(&c->d_sums, sizeof(double) * 3));
+    CKCR(dev_malloc(&c->err, sizeof(unsigned)));
+    CKCR(dev_malloc(&c->d_partial, sizeof(double) * 3 * CHECK_BLOCKS));
+    CKCR(dev_malloc(&c->d_sums, sizeof(double) * 3));
     CKCR(cudaMemsetAsync(c->solid, 0, c->node_bytes, c->stream));
     CKCR(cudaMemsetAsync(c->special, 0, std::max<size_t>(1, c->special_words) * 4, c->stream));
     CKCR(cudaMemsetAsync(c->f[1], 0, c->arena_elems * c->esz, c->stream));
@@ -758,8 +797,9 @@ void lbm_destroy(lbm_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& g : c->gexec)
         if (g) cudaGraphExecDestroy(g);
-    for (auto& g : c->gexec1)
-        if (g) cudaGraphExecDestroy(g);
+    for (auto& gk : c->gexecr)
+        for (auto& g : gk)
+            if (g) cudaGraphExecDestroy(g);
     cudaFree(c->f[0]); cudaFree(c->f[1]); cudaFree(c->solid); cudaFree(c->nflags); cudaFree(c->special);
     cudaFree(c->dd); cudaFree(c->d_item_off); cudaFree(c->ctr); cudaFree(c->pstep); cudaFree(c->err);
     cudaFree(c->d_partial); cudaFree(c->d_sums); cudaFree(c->d_stage); cudaFree(c->d_mom);
@@ -867,15 +907,15 @@ int lbm_add_particles(lbm_ctx* c, int dom, int n, const lbm_particle* p) {
     }
     free_particles(c);
     const size_t ns = c->np_slots;
-    CKC(c, cudaMalloc(&c->pstate, sizeof(PartState) * 2 * ns));
-    CKC(c, cudaMalloc(&c->flipmom, sizeof(double) * 2 * 3 * std::max<int64_t>(fo, 1)));
-    CKC(c, cudaMalloc(&c->pst, sizeof(PartStatic) * ns));
-    CKC(c, cudaMalloc(&c->links, sizeof(int32_t) * 2 * std::max<int64_t>(lo, 1)));
-    CKC(c, cudaMalloc(&c->flips, sizeof(int32_t) * 2 * std::max<int64_t>(fo, 1)));
-    CKC(c, cudaMalloc(&c->nlinks, sizeof(int32_t) * 2 * ns));
-    CKC(c, cudaMalloc(&c->nflips, sizeof(int32_t) * 2 * ns));
-    CKC(c, cudaMalloc(&c->diag, sizeof(double) * DIAG_N * ns));
-    CKC(c, cudaMalloc(&c->ljf, sizeof(double) * 2 * 4 * ns));
+    CKC(c, dev_malloc(&c->pstate, sizeof(PartState) * 2 * ns));
+    CKC(c, dev_malloc(&c->flipmom, sizeof(double) * 2 * 3 * std::max<int64_t>(fo, 1)));
+    CKC(c, dev_malloc(&c->pst, sizeof(PartStatic) * ns));
+    CKC(c, dev_malloc(&c->links, sizeof(int32_t) * 2 * std::max<int64_t>(lo, 1)));
+    CKC(c, dev_malloc(&c->flips, sizeof(int32_t) * 2 * std::max<int64_t>(fo, 1)));
+    CKC(c, dev_malloc(&c->nlinks, sizeof(int32_t) * 2 * ns));
+    CKC(c, dev_malloc(&c->nflips, sizeof(int32_t) * 2 * ns));
+    CKC(c, dev_malloc(&c->diag, sizeof(double) * DIAG_N * ns));
+    CKC(c, dev_malloc(&c->ljf, sizeof(double) * 2 * 4 * ns));
     CKC(c, cudaMemset(c->ljf, 0, sizeof(double) * 2 * 4 * ns));
     CKC(c, cudaMemset(c->nlinks, 0, sizeof(int32_t) * 2 * ns));
     CKC(c, cudaMemset(c->nflips, 0, sizeof(int32_t) * 2 * ns));
@@ -900,10 +940,20 @@ int lbm_add_particles(lbm_ctx* c, int dom, int n, const lbm_particle* p) {
     return sync_and_check(c);
 }
 
+// Wait for the work queued so far and clear the sticky device error word:
+// the caller is about to replace the state those steps produced.
+int clear_errors(lbm_ctx* c) {
+    CKC(c, cudaStreamSynchronize(c->stream));
+    CKC(c, cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    return LBM_OK;
+}
+
 int lbm_set_populations(lbm_ctx* c, int dom, const double* f) {
     int r = check_dom(c, dom);
     if (r) return r;
     if (!f) return fail(c, LBM_E_INVAL, "population array is NULL");
+    r = clear_errors(c);
+    if (r) return r;
     const DomDev& D = c->hd[dom];
     const size_t bytes = sizeof(double) * 9 * (size_t)D.nx * D.ny;
     r = ensure_stage(c, bytes);
@@ -940,10 +990,9 @@ int lbm_step(lbm_ctx* c, int64_t nsteps) {
         CKC(c, cudaGraphLaunch(c->gexec[c->cur], c->stream));
         left -= GRAPH_STEPS;
     }
-    while (left > 0) {
-        CKC(c, cudaGraphLaunch(c->gexec1[c->cur], c->stream));
-        c->cur ^= 1;
-        --left;
+    if (left > 0) {
+        CKC(c, cudaGraphLaunch(c->gexecr[c->cur][left], c->stream));
+        c->cur ^= (int)(left & 1);
     }
     c->steps += nsteps;
     c->pstate_evt = c->np_active > 0;
@@ -993,7 +1042,7 @@ int lbm_moments_async(lbm_ctx* c, int dom) {
         c->d_mom = nullptr;
         c->h_mom = nullptr;
         c->mom_elems = 0;
-        CKC(c, cudaMalloc(&c->d_mom, sizeof(float) * 3 * n));
+        CKC(c, dev_malloc(&c->d_mom, sizeof(float) * 3 * n));
         CKC(c, cudaMallocHost(&c->h_mom, sizeof(float) * 3 * n));
         c->mom_elems = 3 * n;
     }
@@ -1127,7 +1176,7 @@ int lbm_save(lbm_ctx* c, const char* path) {
 int lbm_load(lbm_ctx* c, const char* path) {
     if (!c || !path) return LBM_E_INVAL;
     c->pstate_evt = false;
-    int r = sync_and_check(c);
+    int r = clear_errors(c);
     if (r) return r;
     FILE* fp = fopen(path, "rb");
     if (!fp) return fail(c, LBM_E_IO, std::string("cannot open ") + path);
@@ -1184,16 +1233,16 @@ int lbm_load(lbm_ctx* c, const char* path) {
         free_particles(c);
         c->hst = hst;
         c->hstate = s;
-        CKC(c, cudaMalloc(&c->pstate, sizeof(PartState) * 2 * ns));
-        CKC(c, cudaMalloc(&c->flipmom, 2 * 8 * fm.size()));
-        CKC(c, cudaMalloc(&c->pst, sizeof(PartStatic) * ns));
-        CKC(c, cudaMalloc(&c->links, 2 * 4 * L.size()));
-        CKC(c, cudaMalloc(&c->flips, 2 * 4 * F.size()));
-        CKC(c, cudaMalloc(&c->nlinks, 2 * 4 * ns));
-        CKC(c, cudaMalloc(&c->nflips, 2 * 4 * ns));
+        CKC(c, dev_malloc(&c->pstate, sizeof(PartState) * 2 * ns));
+        CKC(c, dev_malloc(&c->flipmom, 2 * 8 * fm.size()));
+        CKC(c, dev_malloc(&c->pst, sizeof(PartStatic) * ns));
+        CKC(c, dev_malloc(&c->links, 2 * 4 * L.size()));
+        CKC(c, dev_malloc(&c->flips, 2 * 4 * F.size()));
+        CKC(c, dev_malloc(&c->nlinks, 2 * 4 * ns));
+        CKC(c, dev_malloc(&c->nflips, 2 * 4 * ns));
         const int64_t pr = h.steps & 1;  // the lists of the restored step
-        CKC(c, cudaMalloc(&c->diag, 8 * ns * DIAG_N));
-        CKC(c, cudaMalloc(&c->ljf, sizeof(double) * 2 * 4 * ns));
+        CKC(c, dev_malloc(&c->diag, 8 * ns * DIAG_N));
+        CKC(c, dev_malloc(&c->ljf, sizeof(double) * 2 * 4 * ns));
         CKC(c, cudaMemset(c->ljf, 0, sizeof(double) * 2 * 4 * ns));
         CKC(c, cudaMemcpy(c->pstate, s.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
         CKC(c, cudaMemcpy(c->pstate + ns, s.data(), sizeof(PartState) * ns, cudaMemcpyHostToDevice));
@@ -1359,10 +1408,11 @@ int lbm_autotune(lbm_ctx* c, int trial_steps) {
     // a grid of resident CTAs only (3) holds every SM for the whole pass: in a
     // step with particles the particle launches then wait for the pass to end
     // (measured slower there), so it is tried only without particles
+    // The staged bulk-copy kernel (2) is not a candidate: measured on every
+    // workload and storage kind it ran slower than the register kernel, so it
+    // stays a variant that lbm_set_launch selects explicitly.
     for (int mode : {0, 1, 3, 4})
         if (c->np_active == 0 || mode != 3) cands.push_back({mode, 128, 0});
-    for (Cand k : {Cand{2, 32, 1}, Cand{2, 64, 1}, Cand{2, 64, 2}, Cand{2, 128, 1}, Cand{2, 128, 2}, Cand{2, 256, 1}})
-        if (staged_blocks_per_sm(c->kind, c->noise, c->pl, k.block, k.stages) > 0) cands.push_back(k);
     cudaEvent_t e0, e1;
     CKC(c, cudaEventCreate(&e0));
     CKC(c, cudaEventCreate(&e1));
@@ -1412,6 +1462,20 @@ int lbm_set_launch(lbm_ctx* c, int32_t kernel, int32_t block, int32_t stages) {
     return LBM_OK;
 }
 
+int lbm_set_wait_limit(lbm_ctx* c, uint64_t ns) {
+    if (!c) return LBM_E_INVAL;
+    if (ns > 60ull * 1000000000ull) return fail(c, LBM_E_INVAL, "wait limit above 60 s");
+    c->wait_ns = ns;
+    c->graph_dirty = true;  // the limit travels with each launch
+    return LBM_OK;
+}
+
+int lbm_debug_fail_alloc(int32_t nth) {
+    if (nth < 0) return LBM_E_INVAL;
+    g_fail_alloc.store(nth);
+    return LBM_OK;
+}
+
 int lbm_get_launch(const lbm_ctx* c, int64_t* out4) {
     if (!c || !out4) return LBM_E_INVAL;
     out4[0] = c->grid_mode;
@@ -1422,3 +1486,9 @@ int lbm_get_launch(const lbm_ctx* c, int64_t* out4) {
 }
 
 }  // extern "C"
+
+namespace lbmk {
+// The message lbm_last_error(NULL) returns, for entry points that take no
+// context (the calling thread's copy, as for lbm_create).
+void set_global_error(const char* msg) { g_create_error = msg ? msg : ""; }
+}  // namespace lbmk

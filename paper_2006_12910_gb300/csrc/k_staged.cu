@@ -20,8 +20,9 @@
 // Only nodes at x = 0 or nx - 1 read a wrapped source from global memory
 // (periodic x) or take the Zou-He / corner patch (open ends).  Every mbarrier
 // wait is bounded (about one second by the global timer); a wait that runs
-// out sets ERR_TIMEOUT, waits (bounded again) for the warp's copies in flight
-// and ends the warp's work.
+// out sets ERR_TIMEOUT, waits (bounded again, always by the full second) for
+// the warp's copies in flight and ends the warp's work.  The limit of the
+// stage waits comes with the launch (StreamArgs::wait_ns).
 #include "stream_node.cuh"
 
 namespace lbmk {
@@ -70,13 +71,17 @@ __device__ __forceinline__ uint64_t global_ns() {
 constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;  // one second
 constexpr uint32_t WAIT_LIMIT_ITERS = 1u << 26;     // backstop if the timer stalls
 
-// Bounded wait for the phase of parity `parity` of one mbarrier.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// Bounded wait for the phase of parity `parity` of one mbarrier, at most
+// limit_ns of the global timer.  limit_ns == 0 reports expiry at once without
+// looking at the barrier (the context's test setting that makes every stage
+// wait run out; the copies it skipped are still drained with the full limit).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    if (limit_ns == 0) return false;
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0; it < WAIT_LIMIT_ITERS; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
@@ -88,7 +93,9 @@ __device__ __noinline__ void seam_node(const DomDev& D, const typename S::T* bas
                                        typename S::A* f) {
     typedef typename S::A A;
     const Geo G = load_geo(D);
-    const A inv = (A)(sizeof(A) == 4 ? D.inv_scale_f : D.inv_scale);
+    // scaled half-precision stores stay in their scaled units (collide_node<..., SC>)
+    const A inv = S::SCALED ? (A)1 : (A)(sizeof(A) == 4 ? D.inv_scale_f : D.inv_scale);
+    const A sc = S::SCALED ? (A)(sizeof(A) == 4 ? D.scale_f : D.scale) : (A)1;
     int ym, yp;
     pull_rows(G, y, ym, yp);
 #pragma unroll
@@ -104,8 +111,8 @@ __device__ __noinline__ void seam_node(const DomDev& D, const typename S::T* bas
                 f[i] = (A)0;
         }
     }
-    if (fl & NF_ZH_IN) zou_he<A>(f, 0, zou_he_excess<A>(D, 0));
-    else if (fl & NF_ZH_OUT) zou_he<A>(f, 1, zou_he_excess<A>(D, 1));
+    if (fl & NF_ZH_IN) zou_he<A>(f, 0, zou_he_excess<A>(D, 0) * sc);
+    else if (fl & NF_ZH_OUT) zou_he<A>(f, 1, zou_he_excess<A>(D, 1) * sc);
 }
 
 // Mailbox writes of one node (flag bits 1..8), out of line.
@@ -117,7 +124,8 @@ __device__ __noinline__ void mail_call(const DomDev& D, typename S::T* obase, in
     A v[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) v[i] = f[i];
-    mail_node<S>(G, obase, x, y, fl, v, (A)(sizeof(A) == 4 ? D.scale_f : D.scale));
+    // f is in the store's scaled units when S::SCALED: written without scaling
+    mail_node<S>(G, obase, x, y, fl, v, S::SCALED ? (A)1 : (A)(sizeof(A) == 4 ? D.scale_f : D.scale));
 }
 
 template <class S>
@@ -275,10 +283,12 @@ __global__ void __launch_bounds__(STAGED_MAX_BLOCK) k_stream_staged(StreamArgs a
         T* orow = obase + y * pitch + xs;
         const HotPrm<A> H = load_hot<A>(D);
         const ExtPrm<A> X = load_ext<A, NOISE, PL>(D);
-        const A inv = H.inv_scale;
+        // scaled half-precision stores stay in their scaled units, as in the register kernel
+        const A inv = S::SCALED ? (A)1 : H.inv_scale;
+        const A osc = S::SCALED ? (A)1 : H.scale;
         int ym, yp;
         pull_rows(G, y, ym, yp);
-        const bool done = mbar_wait_bounded(smem_u32(bars + sc), (phase >> sc) & 1u);
+        const bool done = mbar_wait_bounded(smem_u32(bars + sc), (phase >> sc) & 1u, a.wait_ns);
         if (__any_sync(0xffffffffu, !done)) {
             aborted = true;
             break;
@@ -308,12 +318,12 @@ __global__ void __launch_bounds__(STAGED_MAX_BLOCK) k_stream_staged(StreamArgs a
 #pragma unroll
                 for (int i = 0; i < 9; ++i) f[i] = t[i];
             }
-            ok &= collide_node<A, S::SHIFT, NOISE, PL>(f, H, X, (uint32_t)(y * nx + x), step);
+            ok &= collide_node<A, S::SHIFT, NOISE, PL, S::SCALED>(f, H, X, (uint32_t)(y * nx + x), step);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) from_a(f[i], H.scale, orow[(int64_t)i * plane + j]);
+            for (int i = 0; i < 9; ++i) from_a(f[i], osc, orow[(int64_t)i * plane + j]);
             if (fl & 0x1FEu) {
                 if (mail_is_direct(G, x, y)) {
-                    mail_direct<S>(orow + j, plane, pitch, fl, f, H.scale);
+                    mail_direct<S>(orow + j, plane, pitch, fl, f, osc);
                 } else {  // rare: wrapped targets, out of line through a local copy
                     A t[9];
 #pragma unroll
@@ -331,7 +341,7 @@ __global__ void __launch_bounds__(STAGED_MAX_BLOCK) k_stream_staged(StreamArgs a
         // Leave no copy in flight into shared memory this CTA gives up.
         if (lane == 0) atomicOr(a.err, ERR_TIMEOUT);
         for (int s = 0; s < stages; ++s)
-            if (pending & (1u << s)) mbar_wait_bounded(smem_u32(bars + s), (phase >> s) & 1u);
+            if (pending & (1u << s)) mbar_wait_bounded(smem_u32(bars + s), (phase >> s) & 1u, WAIT_LIMIT_NS);
         __syncwarp();
     }
     if (!ok) atomicOr(a.err, ERR_UNSTABLE);

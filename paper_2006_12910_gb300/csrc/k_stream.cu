@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(REG_K1_MAX_BLOCK, (k1_min_blocks<S, NOISE, PL>
 #pragma unroll
         for (int k = 0; k < V; ++k) fl[k] = 0;
         if (special) load_flags<V>(a.nflags + G.node_off + y * pitch + x0, fl);
-        const A inv = H.inv_scale;
+        // scaled half-precision stores stay in their scaled units (see collide_node)
+        const A inv = S::SCALED ? (A)1 : H.inv_scale;
         int ym, yp;
         pull_rows(G, y, ym, yp);
         // x-1 / x+V across a seam: wrapped when periodic; at open ends any
@@ -103,7 +104,8 @@ __global__ void __launch_bounds__(REG_K1_MAX_BLOCK, (k1_min_blocks<S, NOISE, PL>
             const int row = cy(i) == 1 ? ym : (cy(i) == -1 ? yp : y);
             const T* p = base + (int64_t)i * plane + row * pitch;
             A v[V];
-            load_vec<S>(p + x0, v, inv);
+            if constexpr (S::SCALED) load_vec_raw<S>(p + x0, v);
+            else load_vec<S>(p + x0, v, inv);
             if (cx(i) == 0) {
 #pragma unroll
                 for (int k = 0; k < V; ++k) f[i][k] = v[k];

@@ -37,6 +37,9 @@ struct StreamArgs {
     const int64_t* fliptag;
     int64_t fliptag_stride;
     double* flipmom;
+    // Limit of the staged kernel's stage waits in global-timer nanoseconds
+    // (1e9 by default; 0 makes every stage wait report expiry at once).
+    uint64_t wait_ns;
 };
 enum { STREAM_ALL = 0, STREAM_FAR = 1, STREAM_NEAR = 2 };
 
@@ -139,5 +142,8 @@ constexpr int PL_STEP_LJ = PL_LJ | PL_ADVANCE | PL_AHEAD;
 // PL_LJ | PL_ADVANCE (Eq. MP2 at t+1)
 constexpr int PL_SETUP_R = PL_RASTER | PL_MARK | PL_ADVANCE;
 cudaError_t launch_particle_step(int kind, const PartArgs& a, int modes, cudaStream_t s);
+
+// The thread's message for lbm_last_error(NULL) (capi.cu).
+void set_global_error(const char* msg);
 
 }  // namespace lbmk

@@ -110,6 +110,34 @@ __device__ __forceinline__ void store_vec(typename S::T* p, const typename S::A*
     for (int k = 0; k < S::V; ++k) from_a(in[k], scale, r.t[k]);
     *reinterpret_cast<VT*>(p) = r.u;
 }
+// The register stream-collide kernel keeps the scaled half-precision stores
+// in their scaled units through the collision (collide_node<..., SC = true>):
+// loads and stores then only convert, two values per instruction where the
+// hardware packs them.
+template <class S>
+__device__ __forceinline__ void load_vec_raw(const typename S::T* p, float* out) {
+    static_assert(S::SCALED && S::V == 4, "raw half-precision loads cover 4-node chunks");
+    union { uint2 u; typename S::T t[4]; } r;
+    r.u = __ldg(reinterpret_cast<const uint2*>(p));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k] = to_a(r.t[k], 1.0f);
+}
+__device__ __forceinline__ uint32_t pack2(float a, float b, __half) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t pack2(float a, float b, __nv_bfloat16) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+template <class S>
+__device__ __forceinline__ void store_vec_raw(typename S::T* p, const float* in) {
+    static_assert(S::SCALED && S::V == 4, "raw half-precision stores cover 4-node chunks");
+    uint2 u;
+    u.x = pack2(in[0], in[1], typename S::T());
+    u.y = pack2(in[2], in[3], typename S::T());
+    *reinterpret_cast<uint2*>(p) = u;
+}
 template <class S>
 __device__ __forceinline__ typename S::A load_one(const typename S::T* p, typename S::A inv) {
     return to_a(__ldg(p), inv);
@@ -306,25 +334,33 @@ __device__ __forceinline__ void relax_pair(A& fi, A& fo, A e, A w, A usq, A R, A
     }
 }
 
-template <typename A, bool SHIFT, bool NOISE, bool PL>
+// SC (shifted stores only): f holds (f - w_i rho0) * s in the store's scaled
+// units, s = H.scale, and so does the result; the moments are unscaled once
+// per node (exact: s is a power of two) instead of every population.
+template <typename A, bool SHIFT, bool NOISE, bool PL, bool SC = false>
 __device__ __forceinline__ bool collide_node(A f[9], const HotPrm<A>& H, const ExtPrm<A>& X, uint32_t node,
                                              uint32_t step) {
+    static_assert(!SC || SHIFT, "scaled units are those of the shifted stores");
     const A a = (f[1] + f[5]) + f[8];  // e_x > 0
     const A b = (f[3] + f[6]) + f[7];  // e_x < 0
     const A c = (f[2] + f[5]) + f[6];  // e_y > 0
     const A d = (f[4] + f[7]) + f[8];  // e_y < 0
-    const A s = (f[0] + (f[2] + f[4])) + (a + b);
-    const A jx = a - b, jy = c - d;
+    const A s_ = (f[0] + (f[2] + f[4])) + (a + b);
+    const A jx_ = a - b, jy_ = c - d;
+    // unscaled moments (SC: one multiply each by the power of two 1/s)
+    const A s = SC ? s_ * H.inv_scale : s_;
+    const A jx = SC ? jx_ * H.inv_scale : jx_, jy = SC ? jy_ * H.inv_scale : jy_;
     const A rho = SHIFT ? H.rho0 + s : s;
     const A drho = SHIFT ? s : s - H.rho0;
     const bool ok = (rho > (A)0) && (rho < (A)1e30);
     const A irho = rcp_rho<A>(rho);
     A omega = H.omega, om = H.om, tgx = H.tgx, tgy = H.tgy;
     if (PL) {
-        const A sxy = (f[5] + f[7]) - (f[6] + f[8]);
+        const A u1 = SC ? H.inv_scale : (A)1;  // unscaled second moments
+        const A sxy = ((f[5] + f[7]) - (f[6] + f[8])) * u1;
         const A iso = SHIFT ? drho * (A)(1.0 / 3.0) : rho * (A)(1.0 / 3.0);
-        const A pxx = (a + b) - iso - jx * jx * irho;
-        const A pyy = (c + d) - iso - jy * jy * irho;
+        const A pxx = (a + b) * u1 - iso - jx * jx * irho;
+        const A pyy = (c + d) * u1 - iso - jy * jy * irho;
         const A pxy = sxy - jx * jy * irho;
         const A det = pxy * pxy - pxx * pyy;
         const A Astr = (A)3 * sqrt(fabs(det)) * irho;
@@ -337,8 +373,9 @@ __device__ __forceinline__ bool collide_node(A f[9], const HotPrm<A>& H, const E
     const A ux = (jx + rho * tgx) * irho;
     const A uy = (jy + rho * tgy) * irho;
     const A usq = (A)1.5 * (ux * ux + uy * uy);
-    const A R = SHIFT ? omega * rho : rho;
-    const A B = SHIFT ? omega * drho : rho;
+    // in the units of f (SC: times s)
+    const A R = SHIFT ? (SC ? omega * rho * H.scale : omega * rho) : rho;
+    const A B = SHIFT ? omega * (SC ? s_ : drho) : rho;
     const A R3 = (A)3 * R;
     if (SHIFT) f[0] = om * f[0] + (A)wgt(0) * (B - R * usq);
     else f[0] = f[0] + omega * ((A)wgt(0) * (B - R * usq) - f[0]);
@@ -350,7 +387,8 @@ __device__ __forceinline__ bool collide_node(A f[9], const HotPrm<A>& H, const E
         if (X.kT > (A)0) {
             A th[6];
             thetas<A>(node, step, X.dom_id, X.seed, th);
-            const A amp = sqrt(rho * X.kT * omega * ((A)2 - omega) * (A)3);
+            const A amp = SC ? sqrt(rho * X.kT * omega * ((A)2 - omega) * (A)3) * H.scale
+                             : sqrt(rho * X.kT * omega * ((A)2 - omega) * (A)3);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 A z = (A)0;

@@ -66,8 +66,11 @@ struct alignas(16) DomDev {
 // from in the next step.  Pulls therefore need no patching, except at the
 // wall-corner nodes of open ends (NF_CORNER: the directions whose source lies
 // beyond the x range take the node's own opposite slot) and on the Zou-He
-// columns.  A chunk whose nodes all have zero flags takes the plain vector
-// path without reading them.
+// columns.  On a solid node bits 1..8 mark instead which of its slots are
+// mailboxes (slot i, when the node x + e_i is fluid); no fluid node ever reads
+// the other slots of a solid node, so a chunk may overwrite those with its
+// vector stores.  A chunk whose nodes all have zero flags takes the plain
+// vector path without reading them.
 enum : uint16_t {
     NF_SOLID = 1u << 0,
     NF_ZH_IN = 1u << 9,    // Zou-He inlet node (x = 0)

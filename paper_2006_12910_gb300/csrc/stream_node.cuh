@@ -125,7 +125,9 @@ __device__ __noinline__ bool slow_node(const DomDev& D, int x, int y, const type
     if (fl & NF_SOLID) return true;  // solid slots are mailboxes, written by their fluid neighbours
     const HotPrm<A> H = load_hot<A>(D);
     const ExtPrm<A> X = load_ext<A, NOISE, PL>(D);
-    const A inv = H.inv_scale;
+    // scaled half-precision stores stay in their scaled units (see collide_node)
+    constexpr bool SC = S::SCALED;
+    const A inv = SC ? (A)1 : H.inv_scale, osc = SC ? (A)1 : H.scale;
     A f[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -141,12 +143,13 @@ __device__ __noinline__ bool slow_node(const DomDev& D, int x, int y, const type
         else if (unknown) f[i] = (A)0;
         else f[i] = load_one<S>(base + (int64_t)i * G.plane + (int64_t)sy * G.pitch + sx, inv);
     }
-    if (fl & NF_ZH_IN) zou_he<A>(f, 0, zou_he_excess<A>(D, 0));
-    else if (fl & NF_ZH_OUT) zou_he<A>(f, 1, zou_he_excess<A>(D, 1));
-    const bool ok = collide_node<A, S::SHIFT, NOISE, PL>(f, H, X, (uint32_t)((int64_t)y * G.nx + x), step);
+    const A zsc = SC ? H.scale : (A)1;
+    if (fl & NF_ZH_IN) zou_he<A>(f, 0, zou_he_excess<A>(D, 0) * zsc);
+    else if (fl & NF_ZH_OUT) zou_he<A>(f, 1, zou_he_excess<A>(D, 1) * zsc);
+    const bool ok = collide_node<A, S::SHIFT, NOISE, PL, SC>(f, H, X, (uint32_t)((int64_t)y * G.nx + x), step);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) from_a(f[i], H.scale, obase[(int64_t)i * G.plane + ni]);
-    if (fl & 0x1FEu) mail_node<S>(G, obase, x, y, fl, f, H.scale);
+    for (int i = 0; i < 9; ++i) from_a(f[i], osc, obase[(int64_t)i * G.plane + ni]);
+    if (fl & 0x1FEu) mail_node<S>(G, obase, x, y, fl, f, osc);
     return ok;
 }
 
@@ -204,14 +207,22 @@ __device__ __forceinline__ bool finish_chunk(const StreamArgs& a, const DomDev& 
                                              uint32_t step, bool near_item, int32_t next_stamp) {
     typedef typename S::A A;
     constexpr int V = S::V;
+    // scaled half-precision stores: f holds scaled values (see collide_node),
+    // so loads and stores here convert without scaling
+    constexpr bool SC = S::SCALED;
+    const A io_inv = SC ? (A)1 : H.inv_scale, io_scale = SC ? (A)1 : H.scale;
     const int64_t pitch = G.pitch, plane = G.plane;
     bool ok = true;
-    uint32_t solid_bits = 0, any = 0;
+    // any: OR of the fluid nodes' flags (mailbox writes, open-column patches);
+    // mb_planes: planes in which a solid node of the chunk has a mailbox slot
+    uint32_t solid_bits = 0, any = 0, mb_planes = 0;
     if (special) {
 #pragma unroll
         for (int k = 0; k < V; ++k) {
-            any |= fl[k];
-            solid_bits |= (uint32_t)(fl[k] & NF_SOLID) << k;
+            const bool sol = fl[k] & NF_SOLID;
+            solid_bits |= (uint32_t)sol << k;
+            if (sol) mb_planes |= fl[k];
+            else any |= fl[k];
         }
         if (any & (NF_ZH_IN | NF_ZH_OUT | NF_CORNER)) {
 #pragma unroll
@@ -221,14 +232,14 @@ __device__ __forceinline__ bool finish_chunk(const StreamArgs& a, const DomDev& 
 #pragma unroll
                     for (int i = 1; i < 9; ++i)
                         if ((x == 0 && cx(i) == 1) || (x == G.nx - 1 && cx(i) == -1))
-                            f[i][k] = load_one<S>(base + (int64_t)opp(i) * plane + y * pitch + x, H.inv_scale);
+                            f[i][k] = load_one<S>(base + (int64_t)opp(i) * plane + y * pitch + x, io_inv);
                 }
                 if (fl[k] & (NF_ZH_IN | NF_ZH_OUT)) {
                     A n9[9];
 #pragma unroll
                     for (int i = 0; i < 9; ++i) n9[i] = f[i][k];
                     const int side = (fl[k] & NF_ZH_IN) ? 0 : 1;
-                    zou_he<A>(n9, side, zou_he_excess<A>(D, side));
+                    zou_he<A>(n9, side, SC ? zou_he_excess<A>(D, side) * H.scale : zou_he_excess<A>(D, side));
 #pragma unroll
                     for (int i = 0; i < 9; ++i) f[i][k] = n9[i];
                 }
@@ -240,31 +251,38 @@ __device__ __forceinline__ bool finish_chunk(const StreamArgs& a, const DomDev& 
         A n9[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) n9[i] = f[i][k];
-        const bool rok = collide_node<A, S::SHIFT, NOISE, PL>(n9, H, X, (uint32_t)(y * G.nx + x0 + k), step);
+        const bool rok = collide_node<A, S::SHIFT, NOISE, PL, SC>(n9, H, X, (uint32_t)(y * G.nx + x0 + k), step);
         ok &= rok || ((solid_bits >> k) & 1u);  // solid nodes compute on mailbox values and are discarded
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i][k] = n9[i];
     }
     typename S::T* orow = obase + y * pitch + x0;
-    if (solid_bits == 0) {
+    // A plane in which no solid node of the chunk has a mailbox slot is stored
+    // whole (the solid nodes' slots there are read by nobody); otherwise the
+    // fluid nodes are stored one by one.  A chunk of solid nodes only stores
+    // nothing.
+    if (solid_bits != (1u << V) - 1u) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) store_vec<S>(orow + (int64_t)i * plane, f[i], H.scale);
-    } else {
+        for (int i = 0; i < 9; ++i) {
+            if (!((mb_planes >> i) & 1u)) {
+                if constexpr (SC) store_vec_raw<S>(orow + (int64_t)i * plane, f[i]);
+                else store_vec<S>(orow + (int64_t)i * plane, f[i], H.scale);
+            } else {
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-#pragma unroll
-            for (int k = 0; k < V; ++k)
-                if (!((solid_bits >> k) & 1u)) from_a(f[i][k], H.scale, orow[(int64_t)i * plane + k]);
+                for (int k = 0; k < V; ++k)
+                    if (!((solid_bits >> k) & 1u)) from_a(f[i][k], io_scale, orow[(int64_t)i * plane + k]);
+            }
+        }
     }
     if (any & 0x1FEu) {
 #pragma unroll
         for (int k = 0; k < V; ++k) {
-            if (fl[k] & 0x1FEu) {
+            if ((fl[k] & 0x1FEu) && !(fl[k] & NF_SOLID)) {
                 A n9[9];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) n9[i] = f[i][k];
-                if (mail_is_direct(G, x0 + k, y)) mail_direct<S>(orow + k, plane, pitch, fl[k], n9, H.scale);
-                else mail_node<S>(G, obase, x0 + k, y, fl[k], n9, H.scale);
+                if (mail_is_direct(G, x0 + k, y)) mail_direct<S>(orow + k, plane, pitch, fl[k], n9, io_scale);
+                else mail_node<S>(G, obase, x0 + k, y, fl[k], n9, io_scale);
             }
         }
     }

@@ -26,7 +26,7 @@ EXPORTED = [
     "lbm_get_populations", "lbm_step", "lbm_sync", "lbm_moments", "lbm_moments_device", "lbm_moments_async",
     "lbm_moments_async_wait", "lbm_particles", "lbm_particle_forces", "lbm_checks", "lbm_step_count",
     "lbm_save", "lbm_load", "lbm_autotune", "lbm_set_launch", "lbm_get_launch", "lbm_profile_steps", "lbm_time_stream", "lbm_fp64_fma_rate",
-    "lbm_checks_noalloc", "lbm_last_error", "lbm_destroy",
+    "lbm_checks_noalloc", "lbm_set_wait_limit", "lbm_debug_fail_alloc", "lbm_last_error", "lbm_destroy",
 ]
 NOALLOC_MAX_ROWS = 16384
 
@@ -112,6 +112,8 @@ def load(build_if_missing: bool = True):
             "lbm_fp64_fma_rate": (ctypes.c_int, [_vp, _dp]),
             "lbm_checks_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                   ctypes.c_int32, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp]),
+            "lbm_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+            "lbm_debug_fail_alloc": (ctypes.c_int, [ctypes.c_int32]),
             "lbm_last_error": (ctypes.c_char_p, [_vp]),
             "lbm_destroy": (None, [_vp]),
         }
@@ -162,7 +164,7 @@ class Context:
         self.ndom = len(plist)
         arr = (Params * self.ndom)(*plist)
         h = ctypes.c_void_p()
-        s = ctypes.c_void_p(stream) if stream else None
+        s = _stream_ptr(stream)
         if self.ndom == 1:
             rc = self.L.lbm_create(arr, s, ctypes.byref(h))
         else:
@@ -315,9 +317,30 @@ class Context:
         self._ck(self.L.lbm_get_launch(self.h, out))
         return tuple(int(v) for v in out)
 
+    def set_wait_limit(self, ns):
+        """lbm_set_wait_limit: limit of the bounded device waits in ns (0: every stage wait expires at once)."""
+        self._ck(self.L.lbm_set_wait_limit(self.h, int(ns)))
+
+
+def debug_fail_alloc(nth):
+    """lbm_debug_fail_alloc: the nth device allocation from now on fails (0: off)."""
+    r = load().lbm_debug_fail_alloc(int(nth))
+    if r != 0:
+        raise LbmError(r, "lbm_debug_fail_alloc")
+
+
+def _stream_ptr(stream):
+    """A CUDA stream handle from a torch.cuda.Stream (its cuda_stream), an int, or None."""
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    return ctypes.c_void_p(int(stream)) if int(stream) else None
+
 
 def checks_noalloc(d_populations, store, nx, ny, pitch, rho0, store_scale, d_solid, d_out3, stream=None):
-    """lbm_checks_noalloc on caller-owned device buffers (pointers or tensors); returns the status code."""
+    """lbm_checks_noalloc on caller-owned device buffers (pointers or tensors) on `stream` (a
+    torch.cuda.Stream, a raw handle or None); returns the status code."""
     def ptr(t):
         if t is None:
             return None
@@ -325,15 +348,14 @@ def checks_noalloc(d_populations, store, nx, ny, pitch, rho0, store_scale, d_sol
     L = load()
     st = STORES[store] if isinstance(store, str) else int(store)
     return L.lbm_checks_noalloc(ptr(d_populations), st, int(nx), int(ny), int(pitch), float(rho0),
-                                float(store_scale), ptr(d_solid), ptr(d_out3),
-                                ctypes.c_void_p(stream) if stream else None)
+                                float(store_scale), ptr(d_solid), ptr(d_out3), _stream_ptr(stream))
 
 
 def fp64_fma_rate(stream=None):
     """lbm_fp64_fma_rate: the device's FP64 FMA rate in GFLOP/s (2 flops per FMA)."""
     L = load()
     g = ctypes.c_double(0.0)
-    r = L.lbm_fp64_fma_rate(ctypes.c_void_p(stream) if stream else None, ctypes.byref(g))
+    r = L.lbm_fp64_fma_rate(_stream_ptr(stream), ctypes.byref(g))
     if r != 0:
         raise LbmError(r, (L.lbm_last_error(None) or b"").decode())
     return float(g.value)
