@@ -8,15 +8,23 @@ from paper_2006_12910_gb300 import lbm, workloads
 # Storage scale of the shifted half-precision kinds in the tests (power of two).
 HALF_SCALE = 4096.0
 
-# Relative-L2 tolerances after the stated number of steps (see the tests).
+# Relative-L2 tolerances over fluid nodes after the stated number of steps (see the
+# tests): rho and u (the density and velocity criteria), the shifted populations
+# f - omega_i rho0 (fneq: the part that carries the dynamics, undiluted by the rest
+# value omega_i rho0), and rho - rho0 (drho), gated where the oracle's density
+# deviation is resolvable (rms >= DRHO_MIN; a flow from rest in a closed channel keeps
+# rho - rho0 at round-off, where a relative measure means nothing).
 TOL = {
-    "f64": dict(rho=1e-12, u=1e-12, f=1e-12),
-    # unshifted FP32 keeps f ~ omega_i with a 2^-24 ulp, so density drifts ~1e-8 per step
-    "f32": dict(rho=1e-5, u=1e-3, f=1e-5),
-    "f32s": dict(rho=1e-6, u=1e-4, f=1e-6),
-    "f16s": dict(rho=2e-5, u=5e-3, f=2e-5),
-    "bf16s": dict(rho=2e-4, u=5e-2, f=2e-4),
+    "f64": dict(rho=1e-12, u=1e-12, f=1e-12, fneq=1e-11, drho=1e-11),
+    # unshifted FP32 keeps f ~ omega_i with a 2^-24 ulp: every forcing increment of
+    # ~1e-7 loses ~1 % to rounding, so this store cannot meet the FP32 bounds below
+    # (u 1e-4); its bounds are the measured ones and it is reported, not held to them
+    "f32": dict(rho=1e-5, u=1e-3, f=1e-5, fneq=2e-3, drho=1e-2),
+    "f32s": dict(rho=1e-6, u=1e-4, f=1e-6, fneq=5e-5, drho=5e-5),
+    "f16s": dict(rho=2e-5, u=5e-3, f=2e-5, fneq=5e-3, drho=5e-3),
+    "bf16s": dict(rho=2e-4, u=5e-2, f=2e-4, fneq=5e-2, drho=5e-2),
 }
+DRHO_MIN = 1e-4
 
 ORACLE_KEYS = {f[0] for f in oracle.Params._fields_}
 
@@ -52,18 +60,33 @@ def rel(a, b, mask=None):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
-def compare_state(ref, ctx, store, solid=None, scale=1.0):
-    """Relative L2 of rho, u and f over fluid nodes, against the store's tolerance."""
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def compare_state(ref, ctx, store, solid=None, scale=1.0, rho0=1.0):
+    """Relative L2 over fluid nodes, against the store's tolerance: rho and u (the
+    density and velocity criteria), f, and the parts that carry the dynamics --
+    rho - rho0 (drho) and the shifted populations f - omega_i rho0 (fneq), whose
+    errors a comparison of rho ~ 1 and f ~ omega_i would dilute 100-1000 times."""
     fluid = None if solid is None else (np.asarray(solid) == 0)
     r0, ux0, uy0 = ref.moments()
     r1, ux1, uy1 = ctx.moments()
+    f0, f1 = ref.populations(), ctx.populations()
+    rest = (W9 * rho0)[:, None, None]
     e_rho = rel(r1, r0, fluid)
     e_u = rel(np.stack([ux1, uy1]), np.stack([ux0, uy0]), fluid)
-    e_f = rel(ctx.populations(), ref.populations(), fluid)
+    e_f = rel(f1, f0, fluid)
+    e_drho = rel(r1 - rho0, r0 - rho0, fluid)
+    e_fneq = rel(f1 - rest, f0 - rest, fluid)
     t = TOL[store]
-    return dict(rho=e_rho, u=e_u, f=e_f), dict(rho=t["rho"] * scale, u=t["u"] * scale, f=t["f"] * scale)
+    errs = dict(rho=e_rho, u=e_u, f=e_f, drho=e_drho, fneq=e_fneq)
+    tols = {k: t[k] * scale for k in t}
+    dr = (r0 - rho0) if fluid is None else (r0 - rho0)[fluid]
+    if not (np.sqrt(np.mean(dr * dr)) >= DRHO_MIN):
+        del tols["drho"]  # reported only
+    return errs, tols
 
 
 def assert_close(errs, tols, label=""):
-    bad = {k: (errs[k], tols[k]) for k in errs if not (errs[k] <= tols[k])}
+    bad = {k: (errs[k], tols[k]) for k in tols if not (errs[k] <= tols[k])}
     assert not bad, f"{label}: {bad}"

@@ -1,16 +1,20 @@
 """GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
 the same seeded inputs.
 
-Tolerances (relative L2 over fluid nodes): the FP64 GPU path within 1e-12; the
-FP32 stores within 1e-6 on density and 1e-4 on velocity after the stated steps;
-the shifted FP16 / BF16 stores are held to looser, measured bounds (their
-storage rounding is 2^-11 / 2^-8 of the shifted population).  Noise runs are
-compared pointwise over 10 steps within 1e-5.
+Tolerances (relative L2 over fluid nodes, gpu_helpers.TOL): the FP64 GPU path
+within 1e-12 (1e-11 on the shifted populations); the shifted FP32 store within
+1e-6 on density and 1e-4 on velocity after the stated steps (up to 1000), 5e-5
+on f - omega_i rho0 and on rho - rho0; the shifted FP16 / BF16 stores are held
+to looser, measured bounds (their storage rounding is 2^-11 / 2^-8 of the
+shifted population); the unshifted FP32 store is reported against its own
+measured bounds.  Noise runs are compared pointwise over 10 steps, the largest
+difference over the largest shifted population |f - omega_i rho0|, within 1e-5
+for the shifted FP32 store.
 """
 import numpy as np
 import pytest
 
-from gpu_helpers import assert_close, compare_state, gpu_params, oracle_params, pair, rel
+from gpu_helpers import W9, assert_close, compare_state, gpu_params, oracle_params, pair, rel
 from oracle import oracle
 from paper_2006_12910_gb300 import lbm, workloads
 
@@ -157,10 +161,14 @@ def test_fluctuating_lb_10_steps_pointwise(store, tau, errlog):
     ctx.step(10)
     fr, fg = ref.populations(), ctx.populations()
     err = float(np.abs(fg - fr).max() / np.abs(fr).max())
+    fneq = fr - W9[:, None, None]
+    err_neq = float(np.abs(fg - fr).max() / np.abs(fneq).max())
     errs, tols = compare_state(ref, ctx, store)
-    errlog(store=store, pointwise=err, **errs)
-    lim = {"f64": 1e-12, "f32": 1e-5, "f32s": 1e-5, "f16s": 1e-3, "bf16s": 1e-2}[store]
-    assert err < lim
+    errlog(store=store, pointwise=err, pointwise_neq=err_neq, **errs)
+    # unshifted FP32: measured 1.5e-5 (its rounding is 2^-24 of omega_i, not of f - omega_i rho0)
+    lim = {"f64": 1e-12, "f32": 5e-5, "f32s": 1e-5, "f16s": 1e-3, "bf16s": 1e-2}[store]
+    assert err_neq < lim
+    assert_close(errs, tols, store)
 
 
 @pytest.mark.parametrize("store", ["f64", "f32s", "f16s"])
@@ -313,28 +321,30 @@ def test_invalid_calls_raise():
 
 def test_full_size_porous_workload(errlog):
     """The benchmark workload at full size (2048x1024, ~300 obstacles, 20 particles,
-    Zou-He ends, FP32 shifted store), 10 steps, every node compared with the
-    oracle, on each launch shape the benchmark's autotuner may pick for the
-    register kernel (one item per warp, grid-stride over 16 or 8 CTAs per SM,
-    resident-only grid); all must agree bit for bit."""
+    Zou-He ends, FP32 shifted store), 200 steps, every node compared with the
+    oracle (rho within 1e-6, u within 1e-4, f - omega_i rho0 within 5e-5), on each
+    launch shape the benchmark's autotuner may pick for the register kernel (one
+    item per warp, grid-stride over 16 or 8 CTAs per SM, resident-only grid); all
+    must agree bit for bit."""
     w = workloads.porous()
     base = dict(nx=w.nx, ny=w.ny, **w.params)
     f0 = np.empty((9, w.ny, w.nx))
     f0[:] = oracle.feq(1.0, 0.0, 0.0)[:, None, None]
     ref, ctx = pair(base, "f32s", solid=w.solid, particles=w.particles, f0=f0)
     oracle.set_threads(0)
-    ref.step(10)
+    steps = 200
+    ref.step(steps)
     first = None
     for launch in [(1, 128, 0), (0, 128, 0), (3, 128, 0), (4, 128, 0)]:
         if first is not None:
             _, ctx = pair(base, "f32s", solid=w.solid, particles=w.particles, f0=f0)
         ctx.set_launch(*launch)
-        ctx.step(10)
-        errs, _ = compare_state(ref, ctx, "f32s", w.solid)
+        ctx.step(steps)
+        errs, tols = compare_state(ref, ctx, "f32s", w.solid)
         pr, pg = ref.particles(), ctx.particles()
-        perr = max(abs(a[k] - b[k]) for a, b in zip(pr, pg) for k in ("x", "y", "U", "V"))
+        perr = max(abs(a[k] - b[k]) for a, b in zip(pr, pg) for k in ("x", "y", "U", "V", "Omega"))
         errlog(launch=launch, **errs, particle=perr)
-        assert errs["rho"] < 1e-6 and errs["f"] < 1e-6 and errs["u"] < 1e-3
+        assert_close(errs, tols, f"porous {launch}")
         assert perr < 1e-6
         f = ctx.populations()
         if first is None:
