@@ -27,10 +27,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) per full stream-collide launch, from one ncu capture of the
-# current kernel version on this workload's geometry (a pass over every work item).
-# Any change to the kernel voids it.
-NCU_TRAFFIC = {("k_stream_collide", "f32s", 2048, 1024): 105.5e6}
+# DRAM bytes (read + write) per full stream-collide launch come from the ncu summary of
+# the bench workload under profiles/; it records the hash of the CUDA sources it was
+# taken on, and the number is reported only while the sources still hash the same.
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_stream_collide_porous_2048x1024.md")
 
 METRIC = "D2Q9 MLUPS and % HBM roofline, FP32/FP16-store vs FP64 path at stated error"
 # FP64 operations of one BGK collision with the velocity-shift force (unshifted FP64
@@ -41,6 +41,43 @@ METRIC = "D2Q9 MLUPS and % HBM roofline, FP32/FP16-store vs FP64 path at stated 
 FP64_FLOPS_PER_NODE = 97
 UNIT = "MLUPS"
 STORE_BYTES = {"f64": 8, "f32": 4, "f32s": 4, "f16s": 2, "bf16s": 2}
+
+
+def csrc_hash() -> str:
+    """SHA-256 (first 16 hex digits) of the CUDA sources and the C header, in name order."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2006_12910_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    with open(os.path.join(ROOT, "include", "lbm.h"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, store: str):
+    """(bytes per launch, note) from the profile summary when its source hash matches the
+    current sources, else (None, why)."""
+    try:
+        with open(TRAFFIC_PROFILE) as fh:
+            text = fh.read()
+    except OSError:
+        return None, "no profile summary"
+    want = csrc_hash()
+    got, val = None, None
+    for line in text.splitlines():
+        line = line.strip().strip("`")
+        if line.startswith("source_hash:"):
+            got = line.split(":", 1)[1].strip()
+        if line.startswith(f"traffic_bytes_per_launch[{kernel},{store}]:"):
+            val = float(line.split(":", 1)[1].strip())
+    if val is None:
+        return None, "no traffic line for this kernel and store"
+    if got != want:
+        return None, f"profile taken on sources {got}, current {want}"
+    return val, f"ncu, sources {want}"
 
 
 def _peaks():
@@ -379,6 +416,125 @@ def ensemble_bench(lbm, workloads, stream, steps32: int, steps64: int, samples: 
     return out
 
 
+def _timed_steps(ctx, stream, steps):
+    """Device ms of `steps` graph-replayed steps on the context stream (CUDA events)."""
+    import torch
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    ctx.step(steps)
+    a1.record(stream)
+    a1.synchronize()
+    ctx.sync()
+    return a0.elapsed_time(a1)
+
+
+def power_law_bench(lbm, workloads, stream, peak: float, steps: int = 400):
+    """The power-law channel (4096 x 256, walls in y, body force, xi = 0.01, tau* clamped to
+    [0.51, 2.0]) for n = 0.5, 0.75, 1.5 and each store: MLUPS of the graph-replayed step and
+    the HBM fraction of the stream-collide pass (its tau* variant).  Timed from rest over a
+    short window.  At n = 1.5 the clamp holds the fluid at nu = 1/300 everywhere and g = 1e-6
+    would drive the developed flow past Ma 1, so that case runs at g = 2e-8."""
+    out = {}
+    for n in (0.5, 0.75, 1.5):
+        w = workloads.power_law(n, g=2e-8 if n == 1.5 else 1e-6)
+        nodes = w.nx * w.ny
+        row = {"workload": f"power-law channel {w.nx}x{w.ny}: {w.note}"}
+        for store in ("f64", "f32s", "f16s", "bf16s"):
+            scale = 4096.0 if store in ("f16s", "bf16s") else 1.0
+            p = lbm.make_params(nx=w.nx, ny=w.ny, store=store, store_scale=scale, **w.params)
+            ctx = lbm.Context(p, stream=stream.cuda_stream)
+            ctx.autotune(5)
+            ctx.step(50)
+            ctx.sync()
+            ms = _timed_steps(ctx, stream, steps)
+            k1 = ctx.time_stream(50) / 50
+            gbs = nodes * 2 * 9 * STORE_BYTES[store] / (k1 * 1e-3) / 1e9
+            row[store] = {"MLUPS": nodes * steps / (ms * 1e-3) / 1e6, "kernel_ms": k1, "kernel_GBs": gbs,
+                          "frac": gbs / peak, "steps": steps}
+            ctx.close()
+        out[f"n={n}"] = row
+    return out
+
+
+def flb_bench(lbm, workloads, stream, peak: float, steps: int = 2000, samples: int = 40):
+    """The fluctuating-LB configuration (512 x 512 periodic, tau = 1, kT = 1e-5, one R = 5
+    neutrally buoyant disk): MLUPS of the graph-replayed step, the HBM fraction of the
+    stream-collide pass (its noise variant) and the fluid temperature <rho u^2>/kT."""
+    w = workloads.flb()
+    nodes = w.nx * w.ny
+    p = lbm.make_params(nx=w.nx, ny=w.ny, store="f32s", max_particles=1, **w.params)
+    ctx = lbm.Context(p, stream=stream.cuda_stream, particles=[w.particles])
+    ctx.autotune(10)
+    ctx.step(500)
+    ctx.sync()
+    ms = _timed_steps(ctx, stream, steps)
+    k1 = ctx.time_stream(100) / 100
+    gbs = nodes * 72 / (k1 * 1e-3) / 1e9
+    kT = w.params["kT"]
+    acc = np.zeros(2)
+    for _ in range(samples):
+        ctx.step(50)
+        rho, ux, uy = ctx.moments()
+        acc += ((rho * ux * ux).mean() / kT, (rho * uy * uy).mean() / kT)
+    out = {"workload": f"flb {w.nx}x{w.ny}: {w.note}", "nodes": nodes, "steps": steps,
+           "MLUPS": nodes * steps / (ms * 1e-3) / 1e6, "us_per_step": ms * 1e3 / steps,
+           "kernel_ms": k1, "kernel_GBs": gbs, "frac": gbs / peak, "launch": list(ctx.launch()),
+           "fluid_rho_u2_over_kT": (acc / samples).tolist()}
+    ctx.close()
+    return out
+
+
+# ---- error against the FP64 oracle ------------------------------------------------------------
+# The GPU side runs a fresh context from a workload's start for a few steps and keeps the host
+# state; the oracle leg (below, with the CPU baseline) runs the oracle over the same steps and
+# reports relative L2 errors over fluid nodes of rho - rho0, u and the shifted populations
+# f - omega_i rho0 (the parts that carry the dynamics), and the largest particle-state difference.
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def gpu_snapshot(lbm, stream, w, store, steps):
+    scale = 4096.0 if store in ("f16s", "bf16s") else 1.0
+    p = lbm.make_params(nx=w.nx, ny=w.ny, store=store, store_scale=scale,
+                        max_particles=len(w.particles), **w.params)
+    ctx = lbm.Context(p, stream=stream.cuda_stream, solids=[w.solid] if w.solid is not None else None,
+                      particles=[w.particles] if w.particles else None)
+    ctx.step(steps)
+    snap = {"f": ctx.populations(), "mom": ctx.moments(), "parts": ctx.particles(), "steps": steps}
+    ctx.close()
+    return snap
+
+
+def state_errors(ref, snap, solid, rho0=1.0):
+    fluid = np.ones(snap["f"].shape[1:], bool) if solid is None else (np.asarray(solid) == 0)
+
+    def rel(a, b):
+        nb = np.linalg.norm(b)
+        return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a - b))
+    rest = (W9 * rho0)[:, None]
+    r0, ux0, uy0 = (m[fluid] for m in ref["mom"])
+    r1, ux1, uy1 = (m[fluid] for m in snap["mom"])
+    out = {"steps": snap["steps"],
+           "drho": rel(r1 - rho0, r0 - rho0),
+           "u": rel(np.stack([ux1, uy1]), np.stack([ux0, uy0])),
+           "fneq": rel(snap["f"][:, fluid] - rest, ref["f"][:, fluid] - rest)}
+    if ref["parts"]:
+        out["particle"] = max(abs(a[k] - b[k]) for a, b in zip(ref["parts"], snap["parts"])
+                              for k in ("x", "y", "U", "V", "Omega"))
+    return out
+
+
+def oracle_reference(w, steps):
+    """Part of the oracle leg: the FP64 oracle from the workload's start over `steps` steps."""
+    from oracle import oracle
+    oracle.build()
+    keys = {f[0] for f in oracle.Params._fields_}
+    p = oracle.make_params(nx=w.nx, ny=w.ny, **{k: v for k, v in w.params.items() if k in keys})
+    d = oracle.Domain(p, solid=w.solid, particles=w.particles)
+    d.step(steps)
+    return {"f": d.populations(), "mom": d.moments(), "parts": d.particles()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -395,6 +551,10 @@ def main():
     ap.add_argument("--no-channel", action="store_true")
     ap.add_argument("--no-combined", action="store_true")
     ap.add_argument("--no-grains", action="store_true")
+    ap.add_argument("--no-power-law", action="store_true")
+    ap.add_argument("--no-flb", action="store_true")
+    ap.add_argument("--no-errors", action="store_true",
+                    help="skip the error against the FP64 oracle (part of the oracle leg)")
     ap.add_argument("--channel-steps", type=int, default=16000)
     ap.add_argument("--ensemble-steps", type=int, default=4000)
     ap.add_argument("--launch", default=None,
@@ -480,9 +640,10 @@ def main():
     achieved = alg_bytes / (k1_ms * 1e-3) / 1e9
     launch = ctx.launch()
     k1_name = "k_stream_staged" if launch[0] == 2 else "k_stream_collide"
-    traffic = NCU_TRAFFIC.get((k1_name, args.store, w.nx, w.ny))
+    traffic, traffic_note = recorded_traffic(k1_name, args.store) if (w.nx, w.ny) == (2048, 1024) else \
+        (None, "profile covers the 2048x1024 workload only")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": k1_name, "peak_source": peak_kind,
+                "traffic": traffic, "traffic_source": traffic_note, "kernel": k1_name, "peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "kernel_ms": k1_ms,
                 "kernel_timing": f"CUDA events around {n_ts} back-to-back passes over every work item on the context stream",
                 "kernel_ms_in_sequence": kk / args.profile_steps,
@@ -576,14 +737,80 @@ def main():
         from paper_2006_12910_gb300 import workloads as _wl
         comb = combined_bench(lbm, _wl, stream, 200, peak)
 
+    pl = None
+    if rank == 0 and not args.no_power_law:
+        from paper_2006_12910_gb300 import workloads as _wl
+        pl = power_law_bench(lbm, _wl, stream, peak)
+
+    flbk = None
+    if rank == 0 and not args.no_flb:
+        from paper_2006_12910_gb300 import workloads as _wl
+        flbk = flb_bench(lbm, _wl, stream, peak)
+
+    # GPU states for the error against the oracle: (label, workload, store, steps)
+    snaps = []
+    do_err = rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_errors
+    if do_err:
+        from paper_2006_12910_gb300 import workloads as _wl
+        specs = [("headline", w, args.store, 20)]
+        specs += [(f"variant:{st}", w, st, 20) for st in variants]
+        if grains is not None:
+            specs.append(("grains", _wl.grains(), "f32s", 10))
+        if chan is not None:
+            specs.append(("channel", _wl.confined_channel(), "f32s", 10))
+        if comb is not None:
+            specs.append(("combined", _wl.combined(), "f32s", 10))
+        if flbk is not None:
+            specs += [("flb", _wl.flb(), st, 10) for st in ("f32s", "f16s")]
+        if pl is not None:
+            for n in (0.5, 0.75, 1.5):
+                # an x-periodic 64-wide copy of the 256-high channel: the flow is x-invariant
+                wn = _wl.power_law(n, nx=64, ny=256, g=2e-8 if n == 1.5 else 1e-6)
+                specs += [(f"power_law:n={n}", wn, st, 500) for st in ("f64", "f32s", "f16s", "bf16s")]
+        for label, wk, st, k in specs:
+            snaps.append((label, wk, st, gpu_snapshot(lbm, stream, wk, st, k)))
+
     cpu = None
+    errors = {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # ---- the oracle leg: CPU baseline and error against the oracle -----------------------
         v, n, t, cores = cpu_oracle_mlups(w, budget_s=15.0)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{n} timesteps of the full 2048x1024 porous workload, FP64 oracle, OpenMP static"}
         v1, n1, t1, _ = cpu_oracle_mlups(w, budget_s=6.0, threads=1)
         cpu["single_core"] = {"value": v1, "unit": UNIT, "cores": 1,
                               "sample": f"{n1} timesteps of the same workload on one thread"}
+        from paper_2006_12910_gb300 import workloads as _wl
+        wf = _wl.porous(args.nx, args.ny)
+        wf.particles = []
+        v2, n2, t2, _ = cpu_oracle_mlups(wf, budget_s=8.0)
+        cpu["without_particles"] = {"value": v2, "unit": UNIT, "cores": cores,
+                                    "sample": f"{n2} timesteps of the porous workload with its particles "
+                                              "removed (the oracle scans the whole lattice once per particle "
+                                              "for the forces)"}
+        refs = {}
+        for label, wk, st, snap in snaps:
+            key = (wk.name, wk.nx, wk.ny, snap["steps"])
+            if key not in refs:
+                refs[key] = oracle_reference(wk, snap["steps"])
+            errors.setdefault(label, {})[st] = state_errors(refs[key], snap, wk.solid,
+                                                            wk.params.get("rho0", 1.0))
+        snaps.clear()
+        refs.clear()
+        for label, per in errors.items():
+            if label.startswith("variant:"):
+                variants[label.split(":", 1)[1]]["error_vs_oracle"] = per[label.split(":", 1)[1]]
+            elif label == "grains" and grains is not None:
+                grains["error_vs_oracle"] = per["f32s"]
+            elif label == "channel" and chan is not None:
+                chan["error_vs_oracle"] = per["f32s"]
+            elif label == "combined" and comb is not None:
+                comb["error_vs_oracle"] = per["f32s"]
+            elif label == "flb" and flbk is not None:
+                flbk["error_vs_oracle"] = per
+            elif label.startswith("power_law:") and pl is not None:
+                pl[label.split(":", 1)[1]]["error_vs_oracle"] = dict(
+                    per, note="64x256 x-periodic copy of the channel, 500 steps from rest")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -597,7 +824,10 @@ def main():
                                       "grid": launch[3], "graph_steps": 8}},
                 "fluid_node_mlups": value * fluid / nodes,
                 "clocks": clk, "gpu_launches": args.steps * kernels_per_step,
-                "roofline": roofline, "e2e": e2e, "variants": variants, "ensemble": ens, "channel": chan, "grains": grains, "combined": comb, "cpu_baseline": cpu}
+                "roofline": roofline, "e2e": e2e,
+                "error_vs_oracle": errors.get("headline", {}).get(args.store),
+                "variants": variants, "ensemble": ens, "channel": chan, "grains": grains, "combined": comb,
+                "power_law": pl, "flb": flbk, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
