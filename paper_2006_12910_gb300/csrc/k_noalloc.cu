@@ -22,8 +22,10 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <string>
 
 #include "../../include/lbm.h"
+#include "kernels.h"
 #include "lbm_dev.cuh"
 
 namespace lbmk {
@@ -89,26 +91,46 @@ __global__ void k_rows_final(NoallocArgs a) {
 
 }  // namespace lbmk
 
+namespace {
+int noalloc_fail(int code, const char* msg) {
+    lbmk::set_global_error(msg);
+    return code;
+}
+int noalloc_cuda_fail(const char* what, cudaError_t e) {
+    std::string m = std::string("lbm_checks_noalloc: ") + what + ": " + cudaGetErrorString(e);
+    lbmk::set_global_error(m.c_str());
+    return LBM_E_CUDA;
+}
+}  // namespace
+
 extern "C" int lbm_checks_noalloc(const void* d_populations, int32_t store, int32_t nx, int32_t ny, int32_t pitch,
                                   double rho0, double store_scale, const uint8_t* d_solid, double* d_out3,
                                   void* cuda_stream) {
     using namespace lbmk;
-    if (!d_populations || !d_out3) return LBM_E_INVAL;
-    if (nx < 1 || ny < 1 || pitch < nx) return LBM_E_INVAL;
-    if (ny > LBM_NOALLOC_MAX_ROWS) return LBM_E_INVAL;  // more rows than the static scratch holds
-    if ((int64_t)pitch * ny > ((int64_t)1 << 31)) return LBM_E_INVAL;
-    if (store < LBM_F64 || store > LBM_BF16S) return LBM_E_INVAL;
+    if (!d_populations || !d_out3) return noalloc_fail(LBM_E_INVAL, "lbm_checks_noalloc: NULL population or output buffer");
+    if (nx < 1 || ny < 1 || pitch < nx) return noalloc_fail(LBM_E_INVAL, "lbm_checks_noalloc: need nx, ny >= 1 and pitch >= nx");
+    if (ny > LBM_NOALLOC_MAX_ROWS)  // more rows than the static scratch holds
+        return noalloc_fail(LBM_E_INVAL, "lbm_checks_noalloc: ny above LBM_NOALLOC_MAX_ROWS");
+    if ((int64_t)pitch * ny > ((int64_t)1 << 31)) return noalloc_fail(LBM_E_INVAL, "lbm_checks_noalloc: plane above 2^31 elements");
+    if (store < LBM_F64 || store > LBM_BF16S) return noalloc_fail(LBM_E_INVAL, "lbm_checks_noalloc: unknown store kind");
     const bool scaled = store == LBM_F16S || store == LBM_BF16S;
-    if (scaled && !(store_scale > 0.0)) return LBM_E_INVAL;
+    if (scaled && !(store_scale > 0.0)) return noalloc_fail(LBM_E_INVAL, "lbm_checks_noalloc: store_scale must be > 0");
 
+    // An error left pending by earlier work is the caller's, not this call's:
+    // report it without clearing it.
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess) return noalloc_cuda_fail("a CUDA error was pending before the call", pending);
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return LBM_E_CUDA;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_cuda_fail("cudaGetDevice", e);
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return noalloc_fail(LBM_E_CUDA, "lbm_checks_noalloc: device index above 63");
     void* rows = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_rows_mutex);
         if (!g_rows_addr[dev]) {
             void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_rows) != cudaSuccess || !p) return LBM_E_CUDA;
+            e = cudaGetSymbolAddress(&p, g_noalloc_rows);
+            if (e != cudaSuccess || !p) return noalloc_cuda_fail("cudaGetSymbolAddress", e);
             g_rows_addr[dev] = p;
         }
         rows = g_rows_addr[dev];
@@ -132,7 +154,10 @@ extern "C" int lbm_checks_noalloc(const void* d_populations, int32_t store, int3
         case LBM_F16S: k_rows_noalloc<StF16S><<<grid, 256, 0, s>>>(a); break;
         default: k_rows_noalloc<StBF16S><<<grid, 256, 0, s>>>(a); break;
     }
-    if (cudaGetLastError() != cudaSuccess) return LBM_E_CUDA;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_cuda_fail("row-sum launch", e);
     k_rows_final<<<1, 32, 0, s>>>(a);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_cuda_fail("final-sum launch", e);
+    return LBM_OK;
 }

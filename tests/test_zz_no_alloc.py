@@ -27,27 +27,33 @@ def torch_cuda():
     return torch
 
 
-@pytest.mark.parametrize("store", ["f64", "f32s"])
+@pytest.mark.parametrize("store", ["f64", "f32s", "f16s", "bf16s"])
 def test_noalloc_checks_match_context_checks_twice(torch_cuda, store):
     torch = torch_cuda
     nx, ny, pitch = 150, 70, 160
+    scale = 4096.0 if store in ("f16s", "bf16s") else 1.0  # the scaled half kinds store (f - w rho0) * scale
     solid = workloads.disk_mask(nx, ny, [(40.3, 33.1, 9.2), (110.0, 20.5, 6.4)])
-    params = lbm.make_params(nx=nx, ny=ny, periodic_x=1, periodic_y=0, walls_y=1, tau=0.8, gx=3e-5, store=store)
+    params = lbm.make_params(nx=nx, ny=ny, periodic_x=1, periodic_y=0, walls_y=1, tau=0.8, gx=3e-5, store=store,
+                             store_scale=scale)
     ctx = lbm.Context(params, solids=[solid])
     ctx.set_populations(workloads.random_populations(nx, ny, seed=4242, amp=0.02, solid=solid))
-    dtype = torch.float64 if store == "f64" else torch.float32
+    dtype = {"f64": torch.float64, "f32s": torch.float32, "f16s": torch.float16, "bf16s": torch.bfloat16}[store]
     solid_t = torch.zeros((ny, pitch), dtype=torch.uint8, device="cuda")
     solid_t[:, :nx] = torch.from_numpy(solid.astype(np.uint8)).cuda()
+    stream = torch.cuda.Stream()  # a torch stream object is accepted as the stream argument
     for call in range(2):
         ctx.step(7 + 5 * call)
         ref = ctx.checks()
         f = ctx.populations()
-        vals = f if store == "f64" else (f - WEIGHTS[:, None, None]) * (solid == 0)
+        # the stored values (exactly representable: they come from the store's own kind)
+        vals = f if store == "f64" else (f - WEIGHTS[:, None, None]) * (solid == 0) * scale
         buf = torch.zeros((9, ny, pitch), dtype=dtype, device="cuda")
-        buf[:, :, :nx] = torch.from_numpy(vals.astype(np.float64 if store == "f64" else np.float32)).cuda()
+        buf[:, :, :nx] = torch.from_numpy(vals).to(device="cuda", dtype=dtype)
         out = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
-        rc = lbm.checks_noalloc(buf, store, nx, ny, pitch, 1.0, 1.0, solid_t, out)
+        torch.cuda.synchronize()
+        rc = lbm.checks_noalloc(buf, store, nx, ny, pitch, 1.0, scale, solid_t, out, stream=stream)
         assert rc == 0
+        stream.synchronize()
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert abs(got[0] - ref[0]) <= 1e-12 * ref[0], (call, got, ref)
