@@ -523,6 +523,9 @@ int capture_steps(lbm_ctx* c, int k, int nsteps, cudaGraphExec_t* out) {
     e = cudaGraphInstantiate(out, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     CKC(c, e);
+    // Upload the executable graph now: otherwise its first launch does it,
+    // inside whatever the caller times (tens of microseconds per graph).
+    CKC(c, cudaGraphUpload(*out, c->stream));
     return LBM_OK;
 }
 

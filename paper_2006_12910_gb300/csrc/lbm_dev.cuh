@@ -152,30 +152,27 @@ __device__ __forceinline__ float load_one<StBF16S>(const __nv_bfloat16* p, float
 }
 
 // ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
-// 32x32 -> 64-bit multiplies, key bumped by the Weyl constants between rounds.
+// Noise of Sec. 4: counter-based random numbers, uniforms, normal deviates.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    }
-    return c;
+// Uniform in (0,1) from the top 23 bits, ((x >> 9) + 1/2) / 2^23; exact in FP32
+// and FP64.  FP32: the 23 bits as the mantissa of a number in [1, 2), minus 1,
+// plus 2^-24 -- both steps exact, so this is the same value with no integer
+// to float conversion.
+__device__ __forceinline__ float uni23f(uint32_t x) {
+    return (__uint_as_float(0x3F800000u | (x >> 9)) - 1.0f) + 5.9604644775390625e-08f;
 }
-
-// Uniform in (0,1) from the top 23 bits; exact in FP32 and FP64.
-__device__ __forceinline__ float uni23f(uint32_t x) { return (__uint2float_rn(x >> 9) + 0.5f) * 1.1920928955078125e-07f; }
 __device__ __forceinline__ double uni23d(uint32_t x) { return ((double)(x >> 9) + 0.5) * 1.1920928955078125e-07; }
 
+// FP32: the angle 2 pi b is taken as pi + 2 pi (b - 1/2) with b - 1/2 exact, so
+// the hardware sine / cosine work inside [-pi, pi] (absolute error about 4e-7,
+// far inside the noise tolerance); the radius keeps the accurate logarithm,
+// whose argument reaches 1 - 2^-24.
 __device__ __forceinline__ void box_muller(float a, float b, float& z0, float& z1) {
     const float r = sqrtf(-2.0f * logf(a));
     float s, c;
-    sincospif(2.0f * b, &s, &c);
-    z0 = r * c;
-    z1 = r * s;
+    __sincosf(6.28318530717958647692f * (b - 0.5f), &s, &c);
+    z0 = -r * c;
+    z1 = -r * s;
 }
 __device__ __forceinline__ void box_muller(double a, double b, double& z0, double& z1) {
     const double r = sqrt(-2.0 * log(a));
@@ -189,11 +186,28 @@ template <> __device__ __forceinline__ float uni23<float>(uint32_t x) { return u
 template <> __device__ __forceinline__ double uni23<double>(uint32_t x) { return uni23d(x); }
 
 // Theta_3..Theta_8 of Eq. NP2 for one node: counter (node, step, draw, domain).
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit multiplies, key bumped by the Weyl constants between rounds.
+// The two draws of one node (counter words 2 = 0 and 1) run with their rounds
+// interleaved, so that they share the key schedule.
+__device__ __forceinline__ void philox4x32_10_x2(uint4& a, uint4& b, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t alo0 = 0xD2511F53u * a.x, ahi0 = __umulhi(0xD2511F53u, a.x);
+        const uint32_t alo1 = 0xCD9E8D57u * a.z, ahi1 = __umulhi(0xCD9E8D57u, a.z);
+        const uint32_t blo0 = 0xD2511F53u * b.x, bhi0 = __umulhi(0xD2511F53u, b.x);
+        const uint32_t blo1 = 0xCD9E8D57u * b.z, bhi1 = __umulhi(0xCD9E8D57u, b.z);
+        a = make_uint4(ahi1 ^ a.y ^ k0, alo1, ahi0 ^ a.w ^ k1, alo0);
+        b = make_uint4(bhi1 ^ b.y ^ k0, blo1, bhi0 ^ b.w ^ k1, blo0);
+    }
+}
+
 template <typename A>
 __device__ __forceinline__ void thetas(uint32_t node, uint32_t step, uint32_t dom_id, uint64_t seed, A th[6]) {
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const uint4 r0 = philox4x32_10(make_uint4(node, step, 0u, dom_id), k0, k1);
-    const uint4 r1 = philox4x32_10(make_uint4(node, step, 1u, dom_id), k0, k1);
+    uint4 r0 = make_uint4(node, step, 0u, dom_id), r1 = make_uint4(node, step, 1u, dom_id);
+    philox4x32_10_x2(r0, r1, k0, k1);
     box_muller(uni23<A>(r0.x), uni23<A>(r0.y), th[0], th[1]);
     box_muller(uni23<A>(r0.z), uni23<A>(r0.w), th[2], th[3]);
     box_muller(uni23<A>(r1.x), uni23<A>(r1.y), th[4], th[5]);
