@@ -267,6 +267,7 @@ def channel_bench(lbm, workloads, stream, steps: int):
     ctx.sync()
     a0 = torch.cuda.Event(enable_timing=True)
     a1 = torch.cuda.Event(enable_timing=True)
+    busy_device(stream)
     a0.record(stream)
     ctx.step(steps)
     a1.record(stream)
@@ -297,6 +298,7 @@ def grains_bench(lbm, workloads, stream, steps: int, peak: float):
     gbs = fluid * 72 / (k1 * 1e-3) / 1e9
     a0 = torch.cuda.Event(enable_timing=True)
     a1 = torch.cuda.Event(enable_timing=True)
+    busy_device(stream)
     a0.record(stream)
     ctx.step(steps)
     a1.record(stream)
@@ -333,6 +335,7 @@ def combined_bench(lbm, workloads, stream, steps: int, peak: float):
         out.update(kernel_ms=k1, kernel_GBs=gbs, frac=gbs / peak)
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
+        busy_device(stream)
         a0.record(stream)
         ctx.step(steps)
         a1.record(stream)
@@ -367,6 +370,7 @@ def ensemble_bench(lbm, workloads, stream, steps32: int, steps64: int, samples: 
     ctx.sync()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    busy_device(stream)
     e0.record(stream)
     ctx.step(steps32)
     e1.record(stream)
@@ -416,11 +420,21 @@ def ensemble_bench(lbm, workloads, stream, steps32: int, steps64: int, samples: 
     return out
 
 
+def busy_device(stream, cycles: int = 1_000_000):
+    """Keep the stream's device busy (about half a millisecond) before a timed region, so
+    that the host has enqueued the timed launches by the time the start event fires: the
+    events then bracket device work only, not the host's launch latency."""
+    import torch
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(cycles)
+
+
 def _timed_steps(ctx, stream, steps):
     """Device ms of `steps` graph-replayed steps on the context stream (CUDA events)."""
     import torch
     a0 = torch.cuda.Event(enable_timing=True)
     a1 = torch.cuda.Event(enable_timing=True)
+    busy_device(stream)
     a0.record(stream)
     ctx.step(steps)
     a1.record(stream)
@@ -616,6 +630,7 @@ def main():
     time.sleep(0.3)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    busy_device(stream)
     e0.record(stream)
     ctx.step(args.steps)
     e1.record(stream)
@@ -693,6 +708,7 @@ def main():
             c3.sync()
             a0 = torch.cuda.Event(enable_timing=True)
             a1 = torch.cuda.Event(enable_timing=True)
+            busy_device(stream)
             a0.record(stream)
             c3.step(n3)
             a1.record(stream)

@@ -33,6 +33,8 @@ namespace lbmk {
 
 constexpr int PBLOCK = 256;
 constexpr int A_BLOCK = 160;  // role A launched alone: five warps
+constexpr int BC_BLOCK = 256;  // roles B + C (rasterisation, near-item marks)
+constexpr int MAX_WARPS = (PBLOCK > BC_BLOCK ? PBLOCK : BC_BLOCK) / 32;
 
 __device__ __forceinline__ double min_image(double d, int L, bool periodic) {
     if (!periodic) return d;
@@ -158,13 +160,42 @@ __device__ __noinline__ int block_scan(int c, int* sh_warp, int& excl) {
     if (lane == 31) sh_warp[w] = incl;
     __syncthreads();
     int wbase = 0, total = 0;
-    for (int k = 0; k < PBLOCK / 32; ++k) {
+    const int nw = (int)(blockDim.x >> 5);
+    for (int k = 0; k < nw; ++k) {
         if (k < w) wbase += sh_warp[k];
         total += sh_warp[k];
     }
     excl = wbase + incl - c;
     __syncthreads();
     return total;
+}
+
+// Two exclusive block scans at once (the counts packed in one 64-bit word, so
+// one pass of shuffles and barriers); returns both block totals.
+__device__ __noinline__ void block_scan2(int c0, int c1, long long* sh_warp2, int& excl0, int& excl1, int& total0,
+                                         int& total1) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long c = ((long long)c1 << 32) | (unsigned)c0;
+    long long incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) sh_warp2[w] = incl;
+    __syncthreads();
+    long long wbase = 0, total = 0;
+    const int nw = (int)(blockDim.x >> 5);
+    for (int k = 0; k < nw; ++k) {
+        if (k < w) wbase += sh_warp2[k];
+        total += sh_warp2[k];
+    }
+    const long long ex = wbase + incl - c;
+    excl0 = (int)(unsigned)(ex & 0xffffffffll);
+    excl1 = (int)(ex >> 32);
+    total0 = (int)(unsigned)(total & 0xffffffffll);
+    total1 = (int)(total >> 32);
+    __syncthreads();
 }
 
 // Warps 5-7 of role A (96 threads) prepare the LJ-type repulsion as one group
@@ -359,7 +390,7 @@ union SmemU {
 // out, so each launch fetches only its own instructions); role0 >= LO picks
 // the first role of the launch.
 template <class S, int LO, int HI>
-__global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes, int role0) {
+__global__ void __launch_bounds__(LO >= 2 ? BC_BLOCK : PBLOCK) k_particle_step(PartArgs a, int modes, int role0) {
     typedef typename S::A A;
     // 0: forces, exchange and Newton-Euler; 1: Eq. MP2 for the next step;
     // 2: rasterisation; 3: near-item marks
@@ -403,7 +434,8 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
     SmemU& sm = *reinterpret_cast<SmemU*>(smem_raw);
     __shared__ double tot[DIAG_N];
     __shared__ int lj_n, nnear;
-    __shared__ int sh_warp[PBLOCK / 32];
+    __shared__ int sh_warp[MAX_WARPS];
+    __shared__ long long sh_warp2[MAX_WARPS];
     __shared__ int near[MAXNEAR];
     __shared__ DiskF near_d[MAXNEAR];
     if (LO == 0 && role == 0) {
@@ -1039,19 +1071,32 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
         const int x0 = min(bo.x0, bn.x0) - 2, x1 = max(bo.x0 + bo.w, bn.x0 + bn.w) + 1;
         const int y0 = min(bo.y0, bn.y0) - 2, y1 = max(bo.y0 + bo.h, bn.y0 + bn.h) + 1;
         const int seg_w = 32 * D.V;
-        for (int r = threadIdx.x; r <= y1 - y0; r += PBLOCK) {
+        const int lane = threadIdx.x & 31;
+        // Whole warps iterate together (every row has the same segments), so a
+        // warp takes its list slots with one atomic add on the shared counter.
+        const int nrows = y1 - y0 + 1;
+        for (int r0 = threadIdx.x & ~31; r0 < nrows; r0 += (int)blockDim.x) {
+            const int r = r0 + lane;
             int y = y0 + r, xdummy = 0;
-            if (!wrap_node(D, xdummy, y)) continue;
+            const bool row_ok = r < nrows && wrap_node(D, xdummy, y);
             for (int xx = x0;; xx += seg_w) {
                 const int xc = xx < x1 ? xx : x1;
                 int x = xc, yd = 0;
-                if (wrap_node(D, x, yd)) {
-                    const int64_t item = D.item_off + (int64_t)y * D.seg_per_row + x / seg_w;
+                bool need = false;
+                int64_t item = 0;
+                if (row_ok && wrap_node(D, x, yd)) {
+                    item = D.item_off + (int64_t)y * D.seg_per_row + x / seg_w;
                     int32_t* m = a.mark + (int64_t)mpar * a.total_items + item;
-                    if (atomicExch(m, (int32_t)t_next) != (int32_t)t_next) {
-                        const int slot = atomicAdd(a.near_cnt + lpar, 1);
-                        a.near_list[(int64_t)lpar * a.total_items + slot] = (int32_t)item;
-                    }
+                    need = atomicExch(m, (int32_t)t_next) != (int32_t)t_next;
+                }
+                const uint32_t bal = __ballot_sync(0xffffffffu, need);
+                if (bal) {
+                    int base = 0;
+                    if (lane == __ffs(bal) - 1) base = atomicAdd(a.near_cnt + lpar, __popc(bal));
+                    base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+                    if (need)
+                        a.near_list[(int64_t)lpar * a.total_items + base + __popc(bal & ((1u << lane) - 1u))] =
+                            (int32_t)item;
                 }
                 if (xc == x1) break;
             }
@@ -1106,19 +1151,20 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
     const bool use_bm = U.n() <= PB_CAP;
     if (use_bm) {
         // 0 = fluid node in the domain, 1 = solid, 2 = outside the domain;
-        // bnew / bold: inside the disk at t+1 / t.  Tiles of 32 columns x 32
-        // rows, warp w taking rows w, w + 8, w + 16, w + 24: no division, and
-        // four solid-byte loads per thread in flight at once.
+        // bnew / bold: inside the disk at t+1 / t.  Tiles of 32 columns x
+        // 4 nw rows (nw warps), warp w taking rows w, w + nw, w + 2 nw,
+        // w + 3 nw: no division, and four solid-byte loads per thread in
+        // flight at once.
         const DiskF kn = uni.kn, ko = uni.ko;
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
 #pragma unroll 1
         for (int cb = 0; cb < U.w; cb += 32) {
 #pragma unroll 1
-            for (int rb = 0; rb < U.h; rb += 32) {
+            for (int rb = 0; rb < U.h; rb += 4 * nw) {
                 uint8_t stv[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int r = rb + warp + 8 * u, cc = cb + lane;
+                    const int r = rb + warp + nw * u, cc = cb + lane;
                     stv[u] = 2;
                     if (r < U.h && cc < U.w) {
                         int x = U.x0 + cc, y = U.y0 + r;
@@ -1127,7 +1173,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int r = rb + warp + 8 * u, cc = cb + lane;
+                    const int r = rb + warp + nw * u, cc = cb + lane;
                     if (r < U.h && cc < U.w) {
                         const int i = r * U.w + cc, xu = U.x0 + cc, yu = U.y0 + r;
                         sm.B.node_st[i] = stv[u];
@@ -1164,7 +1210,7 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
     // list places every entry, in lattice order: classify and count, scan,
     // then write (from the stored classification when the box has a bitmap).
     const int nU = U.n();
-    const int per = (nU + PBLOCK - 1) / PBLOCK;
+    const int per = (nU + (int)blockDim.x - 1) / (int)blockDim.x;
     const int i0 = (int)threadIdx.x * per, i1 = min(nU, i0 + per);
     bool overlap = false;
     int lcount = 0, fcount = 0;
@@ -1214,9 +1260,8 @@ __global__ void __launch_bounds__(PBLOCK) k_particle_step(PartArgs a, int modes,
             fcount += (r >> 9) & 1u;
         }
     }
-    int lex, fex;
-    const int ltotal = block_scan(lcount, sh_warp, lex);
-    const int ftotal = block_scan(fcount, sh_warp, fex);
+    int lex, fex, ltotal, ftotal;
+    block_scan2(lcount, fcount, sh_warp2, lex, fex, ltotal, ftotal);
 #pragma unroll 1
     for (int i = i0; i < i1 && (lcount | fcount); ++i) {
         int node = 0;
@@ -1279,7 +1324,7 @@ cudaError_t launch_particle_step(int kind, const PartArgs& a, int modes, cudaStr
     const int grid = (r1 - r0 + 1) * a.np;
     // role A alone uses warps 0-4 only (links, covered / uncovered nodes): a
     // smaller CTA finds room sooner beside a running stream-collide pass
-    const int block = r1 == 0 ? A_BLOCK : PBLOCK;
+    const int block = r1 == 0 ? A_BLOCK : (r0 >= 2 ? BC_BLOCK : PBLOCK);
     if (r1 == 0) LBM_PDISPATCH(kind, (k_particle_step<S, 0, 0><<<grid, block, 0, s>>>(a, modes, r0)))
     else if (r0 == 1 && r1 == 1) LBM_PDISPATCH(kind, (k_particle_step<S, 1, 1><<<grid, block, 0, s>>>(a, modes, r0)))
     else if (r0 >= 2) LBM_PDISPATCH(kind, (k_particle_step<S, 2, 3><<<grid, block, 0, s>>>(a, modes, r0)))
