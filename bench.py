@@ -573,9 +573,14 @@ def main():
     ap.add_argument("--ensemble-steps", type=int, default=4000)
     ap.add_argument("--launch", default=None,
                     help="stream-collide kernel,block,stages (e.g. 1,128,0); skips the autotuner")
+    ap.add_argument("--print-hash", action="store_true",
+                    help="print the hash of the CUDA sources (the key of the profile's traffic figure) and exit")
     ap.add_argument("--nx", type=int, default=2048)
     ap.add_argument("--ny", type=int, default=1024)
     args = ap.parse_args()
+    if args.print_hash:
+        print(csrc_hash())
+        return 0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
