@@ -285,9 +285,16 @@ template <> __device__ __forceinline__ double rcp_rho<double>(double r) { return
 // c = 3 xi A^(n-1), is convex for n < 1 and concave for n > 1, so Newton from
 // the bracket end where g > 0 (n < 1) or g < 0 (n > 1) converges monotonically.
 // ---------------------------------------------------------------------------
+// FP32: the hardware base-2 logarithm (x > 0 here: a strain or a relaxation
+// time) and a division by the fast reciprocal inside the Newton steps, whose
+// fixed point (and so the converged tau*) does not depend on how a step is
+// rounded; FP64 keeps the exact operations.
 template <typename A> __device__ __forceinline__ A powa(A x, A e);
-template <> __device__ __forceinline__ float powa<float>(float x, float e) { return exp2f(e * log2f(x)); }
+template <> __device__ __forceinline__ float powa<float>(float x, float e) { return exp2f(e * __log2f(x)); }
 template <> __device__ __forceinline__ double powa<double>(double x, double e) { return exp2(e * log2(x)); }
+template <typename A> __device__ __forceinline__ A divn(A a, A b);
+template <> __device__ __forceinline__ float divn<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double divn<double>(double a, double b) { return a / b; }
 
 template <typename A>
 __device__ __forceinline__ A solve_tau_pl(A Astr, const ExtPrm<A>& P) {
@@ -307,8 +314,8 @@ __device__ __forceinline__ A solve_tau_pl(A Astr, const ExtPrm<A>& P) {
     for (int it = 0; it < 60; ++it) {
         const A p = powa<A>(t, om);
         const A g = t - (A)0.5 - c * p;
-        const A dg = (A)1 - c * om * p / t;
-        A tn = t - g / dg;
+        const A dg = (A)1 - divn<A>(c * om * p, t);
+        A tn = t - divn<A>(g, dg);
         tn = tn < tmin ? tmin : (tn > tmax ? tmax : tn);
         const A dt = tn - t;
         t = tn;
