@@ -3,8 +3,8 @@
 // The context owns every device buffer: two population arenas (the state
 // f*(t) and the next state), per-node solid bytes, the per-chunk slow-path
 // bitmask, the step counters, a sticky error word and the particle arrays.
-// lbm_step replays CUDA graphs of GRAPH_STEPS timesteps (and one graph of
-// the remaining 1 .. GRAPH_STEPS-1 steps); a timestep is
+// lbm_step replays CUDA graphs of 2^j timesteps, j = 0 .. GRAPH_LOG (the
+// binary digits of the step count, largest first); a timestep is
 //   [particle forces + Newton-Euler] -> [link exchange + re-rasterise]
 //   -> [fused pull-stream + collide over every domain]
 // where the two particle kernels are skipped when no domain holds particles.
@@ -25,7 +25,13 @@ using namespace lbmk;
 
 namespace {
 
-constexpr int GRAPH_STEPS = 8;  // even, so a replay returns to the same arena
+// Step graphs hold 1, 2, 4, .. 2^GRAPH_LOG timesteps.  Every graph launch
+// ends with the whole chain drained (the particle launches run one and two
+// steps ahead of the stream-collide passes inside a graph), so fewer, longer
+// graphs keep the overlapped step at its steady rate: lbm_step(n) launches
+// one graph per binary digit of n mod 2^GRAPH_LOG plus n >> GRAPH_LOG of the
+// largest.
+constexpr int GRAPH_LOG = 6;
 thread_local std::string g_create_error = "no error";
 
 // Test hook of lbm_debug_fail_alloc: when positive, the device allocation
@@ -114,11 +120,10 @@ struct lbm_ctx {
     // that launch, so lbm_particles may wait for this event alone.
     cudaEvent_t ev_pstate = nullptr;
     bool pstate_evt = false;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // GRAPH_STEPS steps from state 0 / 1
-    // gexecr[k][r]: r = 1 .. GRAPH_STEPS-1 steps from state k, so that any
-    // lbm_step(n) runs as whole multi-step graphs (the cross-step overlap of
-    // the particle and stream-collide chains holds inside every graph)
-    cudaGraphExec_t gexecr[2][GRAPH_STEPS] = {};
+    // gexec[k][j]: 2^j steps from state k, so that any lbm_step(n) runs as
+    // whole multi-step graphs (the cross-step overlap of the particle and
+    // stream-collide chains holds inside every graph)
+    cudaGraphExec_t gexec[2][GRAPH_LOG + 1] = {};
     bool graph_dirty = true;
     uint64_t wait_ns = 1000000000ull;  // limit of the bounded device waits (lbm_set_wait_limit)
 
@@ -531,9 +536,10 @@ int capture_steps(lbm_ctx* c, int k, int nsteps, cudaGraphExec_t* out) {
 
 int build_graphs(lbm_ctx* c) {
     for (int k = 0; k < 2; ++k) {
-        int r = capture_steps(c, k, GRAPH_STEPS, &c->gexec[k]);
-        for (int n = 1; n < GRAPH_STEPS && !r; ++n) r = capture_steps(c, k, n, &c->gexecr[k][n]);
-        if (r) return r;
+        for (int j = 0; j <= GRAPH_LOG; ++j) {
+            const int r = capture_steps(c, k, 1 << j, &c->gexec[k][j]);
+            if (r) return r;
+        }
     }
     c->graph_dirty = false;
     return LBM_OK;
@@ -798,9 +804,7 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
 void lbm_destroy(lbm_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    for (auto& g : c->gexec)
-        if (g) cudaGraphExecDestroy(g);
-    for (auto& gk : c->gexecr)
+    for (auto& gk : c->gexec)
         for (auto& g : gk)
             if (g) cudaGraphExecDestroy(g);
     cudaFree(c->f[0]); cudaFree(c->f[1]); cudaFree(c->solid); cudaFree(c->nflags); cudaFree(c->special);
@@ -988,14 +992,12 @@ int lbm_step(lbm_ctx* c, int64_t nsteps) {
         int r = build_graphs(c);
         if (r) return r;
     }
-    int64_t left = nsteps;
-    while (left >= GRAPH_STEPS) {
-        CKC(c, cudaGraphLaunch(c->gexec[c->cur], c->stream));
-        left -= GRAPH_STEPS;
-    }
-    if (left > 0) {
-        CKC(c, cudaGraphLaunch(c->gexecr[c->cur][left], c->stream));
-        c->cur ^= (int)(left & 1);
+    for (int64_t n = nsteps >> GRAPH_LOG; n > 0; --n)  // even step counts: the state stays in arena cur
+        CKC(c, cudaGraphLaunch(c->gexec[c->cur][GRAPH_LOG], c->stream));
+    for (int j = GRAPH_LOG - 1; j >= 0; --j) {
+        if (!((nsteps >> j) & 1)) continue;
+        CKC(c, cudaGraphLaunch(c->gexec[c->cur][j], c->stream));
+        if (j == 0) c->cur ^= 1;
     }
     c->steps += nsteps;
     c->pstate_evt = c->np_active > 0;
