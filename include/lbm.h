@@ -134,9 +134,25 @@ int lbm_set_populations(lbm_ctx* ctx, int dom, const double* f);
 int lbm_get_populations(lbm_ctx* ctx, int dom, double* f);
 
 /* Advance every domain by nsteps timesteps (Eqs. e.LB1, MP1-MP8, NP1-NP2,
- * nn5 per step).  Enqueued on the context stream (replayed as a CUDA graph);
+ * nn5 per step).  Enqueued on the context stream (replayed as CUDA graphs:
+ * one graph of exactly nsteps steps when lbm_prepare_steps prepared that
+ * count, else one graph per binary digit of nsteps, up to 64 steps each);
  * returns without waiting. */
 int lbm_step(lbm_ctx* ctx, int64_t nsteps);
+
+/* Set-up for a step count the caller repeats (no paper counterpart): build
+ * the step graphs of exactly nsteps steps (1 .. LBM_PREPARE_MAX_STEPS) from
+ * either state parity now, so that every later lbm_step(nsteps) replays one
+ * graph.  The chains of particle and stream-collide launches overlap across
+ * the steps of one graph but drain at its end, so one graph per call keeps a
+ * call of nsteps steps closest to the steady per-step time.  At most
+ * LBM_PREPARE_SLOTS counts stay prepared (the oldest is dropped); changes of
+ * geometry, particles or launch configuration rebuild them at the next step.
+ * Blocking (capture and upload of the graphs); LBM_E_INVAL for a count out
+ * of range. */
+#define LBM_PREPARE_MAX_STEPS 256
+#define LBM_PREPARE_SLOTS 4
+int lbm_prepare_steps(lbm_ctx* ctx, int64_t nsteps);
 
 /* Wait for the context stream and report device-side errors. */
 int lbm_sync(lbm_ctx* ctx);

@@ -124,6 +124,10 @@ struct lbm_ctx {
     // whole multi-step graphs (the cross-step overlap of the particle and
     // stream-collide chains holds inside every graph)
     cudaGraphExec_t gexec[2][GRAPH_LOG + 1] = {};
+    // step counts prepared by lbm_prepare_steps and their graphs from state
+    // 0 / 1 (index-aligned)
+    std::vector<int64_t> prepared;
+    std::vector<cudaGraphExec_t> gprep[2];
     bool graph_dirty = true;
     uint64_t wait_ns = 1000000000ull;  // limit of the bounded device waits (lbm_set_wait_limit)
 
@@ -413,7 +417,7 @@ PartArgs part_args(lbm_ctx* c, int cur) {
 // with_flips = false leaves out the moments of nodes changing side (a pass
 // that only times the kernel does not need them).
 cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int block, int64_t grid,
-                                   int mode = STREAM_ALL, bool with_flips = true) {
+                                   int mode = STREAM_ALL, bool with_flips = true, bool pdl = false) {
     StreamArgs a;
     a.doms = c->dd;
     a.item_off = c->d_item_off;
@@ -437,7 +441,7 @@ cudaError_t enqueue_stream_collide(lbm_ctx* c, int cur, cudaStream_t s, int bloc
     a.fliptag_stride = (int64_t)std::max<size_t>(1, c->node_bytes);
     a.flipmom = c->flipmom;
     a.dom0 = c->hd[0];
-    return launch_stream_collide(c->kind, c->noise, c->pl, a, block, grid, c->grid_mode == 2 ? c->stages : 0, s);
+    return launch_stream_collide(c->kind, c->noise, c->pl, a, block, grid, c->grid_mode == 2 ? c->stages : 0, s, pdl);
 }
 
 // One timestep in sequence on one stream: with particles, the particle
@@ -473,7 +477,13 @@ cudaError_t enqueue_step(lbm_ctx* c, int cur, cudaStream_t s) {
 // The force launch of t+1 needs nothing from FAR(t): it reads and writes
 // only slots of items near the particles, which NEAR(t) produced.  What the
 // first steps of the graph need from launches of earlier steps ran before it
-// (previous graph or set-up).
+// (previous graph or set-up).  Each NEAR pass is a programmatic dependent of
+// the force launch before it: the force launch signals once the particle
+// states are solved, the NEAR CTAs are then placed while its exchange
+// completes and wait for its completion (and for the edges from the other
+// streams) before they touch memory, which takes the launch latency off the
+// particle chain.  (The same for the FAR passes and the force launches
+// measured no faster.)
 cudaError_t enqueue_graph_chains(lbm_ctx* c, int k, int nsteps, cudaStream_t s) {
     cudaError_t e;
     if ((e = cudaEventRecord(c->ev_fork, s)) != cudaSuccess) return e;
@@ -500,7 +510,8 @@ cudaError_t enqueue_graph_chains(lbm_ctx* c, int k, int nsteps, cudaStream_t s) 
         if ((e = cudaEventRecord(c->ev_rast[st & 1], c->rast_stream)) != cudaSuccess) return e;
         if (st > 0 && (e = cudaStreamWaitEvent(s, c->ev_rast[(st - 1) & 1], 0)) != cudaSuccess) return e;
         if (st > 0 && (e = cudaStreamWaitEvent(s, c->ev_far[(st - 1) & 1], 0)) != cudaSuccess) return e;
-        if ((e = enqueue_stream_collide(c, cur, s, near_block(c), c->near_grid, STREAM_NEAR)) != cudaSuccess) return e;
+        if ((e = enqueue_stream_collide(c, cur, s, near_block(c), c->near_grid, STREAM_NEAR, true, true)) != cudaSuccess)
+            return e;
         if ((e = cudaEventRecord(c->ev_near[st & 1], s)) != cudaSuccess) return e;
     }
     if ((e = cudaEventRecord(c->ev_join, c->far_stream)) != cudaSuccess) return e;
@@ -538,6 +549,11 @@ int build_graphs(lbm_ctx* c) {
     for (int k = 0; k < 2; ++k) {
         for (int j = 0; j <= GRAPH_LOG; ++j) {
             const int r = capture_steps(c, k, 1 << j, &c->gexec[k][j]);
+            if (r) return r;
+        }
+        c->gprep[k].resize(c->prepared.size(), nullptr);
+        for (size_t i = 0; i < c->prepared.size(); ++i) {
+            const int r = capture_steps(c, k, (int)c->prepared[i], &c->gprep[k][i]);
             if (r) return r;
         }
     }
@@ -807,6 +823,9 @@ void lbm_destroy(lbm_ctx* c) {
     for (auto& gk : c->gexec)
         for (auto& g : gk)
             if (g) cudaGraphExecDestroy(g);
+    for (auto& gk : c->gprep)
+        for (auto& g : gk)
+            if (g) cudaGraphExecDestroy(g);
     cudaFree(c->f[0]); cudaFree(c->f[1]); cudaFree(c->solid); cudaFree(c->nflags); cudaFree(c->special);
     cudaFree(c->dd); cudaFree(c->d_item_off); cudaFree(c->ctr); cudaFree(c->pstep); cudaFree(c->err);
     cudaFree(c->d_partial); cudaFree(c->d_sums); cudaFree(c->d_stage); cudaFree(c->d_mom);
@@ -992,6 +1011,14 @@ int lbm_step(lbm_ctx* c, int64_t nsteps) {
         int r = build_graphs(c);
         if (r) return r;
     }
+    for (size_t i = 0; i < c->prepared.size(); ++i) {
+        if (c->prepared[i] != nsteps || i >= c->gprep[c->cur].size() || !c->gprep[c->cur][i]) continue;
+        CKC(c, cudaGraphLaunch(c->gprep[c->cur][i], c->stream));
+        c->cur ^= (int)(nsteps & 1);
+        c->steps += nsteps;
+        c->pstate_evt = c->np_active > 0;
+        return LBM_OK;
+    }
     for (int64_t n = nsteps >> GRAPH_LOG; n > 0; --n)  // even step counts: the state stays in arena cur
         CKC(c, cudaGraphLaunch(c->gexec[c->cur][GRAPH_LOG], c->stream));
     for (int j = GRAPH_LOG - 1; j >= 0; --j) {
@@ -1002,6 +1029,32 @@ int lbm_step(lbm_ctx* c, int64_t nsteps) {
     c->steps += nsteps;
     c->pstate_evt = c->np_active > 0;
     return LBM_OK;
+}
+
+int lbm_prepare_steps(lbm_ctx* c, int64_t nsteps) {
+    if (!c) return LBM_E_INVAL;
+    if (nsteps < 1 || nsteps > LBM_PREPARE_MAX_STEPS)
+        return fail(c, LBM_E_INVAL, "nsteps must be in 1 .. LBM_PREPARE_MAX_STEPS");
+    int r = LBM_OK;
+    for (int64_t n : c->prepared)
+        if (n == nsteps) return c->graph_dirty && (r = build_graphs(c)) ? r : sync_and_check(c);
+    if ((int)c->prepared.size() >= LBM_PREPARE_SLOTS) {  // drop the oldest
+        for (auto& gk : c->gprep) {
+            if (!gk.empty() && gk[0]) cudaGraphExecDestroy(gk[0]);
+            if (!gk.empty()) gk.erase(gk.begin());
+        }
+        c->prepared.erase(c->prepared.begin());
+    }
+    c->prepared.push_back(nsteps);
+    if (c->graph_dirty) {
+        r = build_graphs(c);
+    } else {
+        for (int k = 0; k < 2 && !r; ++k) {
+            c->gprep[k].resize(c->prepared.size(), nullptr);
+            r = capture_steps(c, k, (int)nsteps, &c->gprep[k].back());
+        }
+    }
+    return r ? r : sync_and_check(c);
 }
 
 int lbm_sync(lbm_ctx* c) {

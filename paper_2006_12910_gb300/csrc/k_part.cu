@@ -391,6 +391,9 @@ union SmemU {
 // the first role of the launch.
 template <class S, int LO, int HI>
 __global__ void __launch_bounds__(LO >= 2 ? BC_BLOCK : PBLOCK) k_particle_step(PartArgs a, int modes, int role0) {
+    // A programmatic dependent launch waits here for the kernels before it
+    // (completion and memory flush); otherwise this returns at once.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     typedef typename S::A A;
     // 0: forces, exchange and Newton-Euler; 1: Eq. MP2 for the next step;
     // 2: rasterisation; 3: near-item marks
@@ -682,6 +685,9 @@ __global__ void __launch_bounds__(LO >= 2 ? BC_BLOCK : PBLOCK) k_particle_step(P
             xmid[2] = xm[2];
         }
         __syncthreads();
+        // the stream-collide pass after this launch may be placed on the SMs
+        // now; it waits for this launch's completion before it reads
+        asm volatile("griddepcontrol.launch_dependents;");
         if (forces && warp == 4 && lane < 3) {
             // the link force of Eq. MP1 at the mid-step boundary velocity, beside the exchange
             const int c = lane;
@@ -1311,7 +1317,26 @@ __global__ void __launch_bounds__(LO >= 2 ? BC_BLOCK : PBLOCK) k_particle_step(P
         default: return cudaErrorInvalidValue;        \
     }
 
-cudaError_t launch_particle_step(int kind, const PartArgs& a, int modes, cudaStream_t s) {
+template <class S, int LO, int HI>
+static cudaError_t launch_part(const PartArgs& a, int modes, int role0, int grid, int block, cudaStream_t s, bool pdl) {
+    if (!pdl) {
+        k_particle_step<S, LO, HI><<<grid, block, 0, s>>>(a, modes, role0);
+        return cudaGetLastError();
+    }
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_particle_step<S, LO, HI>, a, modes, role0);
+}
+
+cudaError_t launch_particle_step(int kind, const PartArgs& a, int modes, cudaStream_t s, bool pdl) {
     if (a.np <= 0) return cudaSuccess;
     // the contiguous range of roles the modes ask for; roles inside the
     // range that the modes leave out return at once
@@ -1325,11 +1350,11 @@ cudaError_t launch_particle_step(int kind, const PartArgs& a, int modes, cudaStr
     // role A alone uses warps 0-4 only (links, covered / uncovered nodes): a
     // smaller CTA finds room sooner beside a running stream-collide pass
     const int block = r1 == 0 ? A_BLOCK : (r0 >= 2 ? BC_BLOCK : PBLOCK);
-    if (r1 == 0) LBM_PDISPATCH(kind, (k_particle_step<S, 0, 0><<<grid, block, 0, s>>>(a, modes, r0)))
-    else if (r0 == 1 && r1 == 1) LBM_PDISPATCH(kind, (k_particle_step<S, 1, 1><<<grid, block, 0, s>>>(a, modes, r0)))
-    else if (r0 >= 2) LBM_PDISPATCH(kind, (k_particle_step<S, 2, 3><<<grid, block, 0, s>>>(a, modes, r0)))
-    else return cudaErrorInvalidValue;  // role A or D together with other roles: no such launch
-    return cudaGetLastError();
+    cudaError_t e = cudaErrorInvalidValue;  // role A or D together with other roles: no such launch
+    if (r1 == 0) LBM_PDISPATCH(kind, (e = launch_part<S, 0, 0>(a, modes, r0, grid, block, s, pdl)))
+    else if (r0 == 1 && r1 == 1) LBM_PDISPATCH(kind, (e = launch_part<S, 1, 1>(a, modes, r0, grid, block, s, pdl)))
+    else if (r0 >= 2) LBM_PDISPATCH(kind, (e = launch_part<S, 2, 3>(a, modes, r0, grid, block, s, pdl)))
+    return e;
 }
 
 }  // namespace lbmk

@@ -34,6 +34,9 @@ constexpr int k1_min_blocks() { return (!NOISE && !PL) ? S::MINB : S::MINB_EXT; 
 template <class S, bool NOISE, bool PL, bool FLIPS>
 __global__ void __launch_bounds__(REG_K1_MAX_BLOCK, (k1_min_blocks<S, NOISE, PL>()))
     k_stream_collide(const __grid_constant__ StreamArgs a) {
+    // A programmatic dependent launch waits here for the kernels before it
+    // (completion and memory flush); otherwise this returns at once.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     typedef typename S::T T;
     typedef typename S::A A;
     constexpr int V = S::V;
@@ -125,35 +128,55 @@ __global__ void __launch_bounds__(REG_K1_MAX_BLOCK, (k1_min_blocks<S, NOISE, PL>
     if (!ok) atomicOr(a.err, ERR_UNSTABLE);
 }
 
+template <class S, bool NOISE, bool PL, bool FLIPS>
+static cudaError_t launch_one(const StreamArgs& a, int block, int64_t grid, cudaStream_t s, bool pdl) {
+    if (!pdl) {
+        k_stream_collide<S, NOISE, PL, FLIPS><<<(unsigned)grid, block, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_stream_collide<S, NOISE, PL, FLIPS>, a);
+}
+
 template <class S, bool FLIPS>
-static cudaError_t launch_kind_f(bool noise, bool pl, const StreamArgs& a, int block, int64_t grid, cudaStream_t s) {
-    if (noise && pl) k_stream_collide<S, true, true, FLIPS><<<(unsigned)grid, block, 0, s>>>(a);
-    else if (noise) k_stream_collide<S, true, false, FLIPS><<<(unsigned)grid, block, 0, s>>>(a);
-    else if (pl) k_stream_collide<S, false, true, FLIPS><<<(unsigned)grid, block, 0, s>>>(a);
-    else k_stream_collide<S, false, false, FLIPS><<<(unsigned)grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+static cudaError_t launch_kind_f(bool noise, bool pl, const StreamArgs& a, int block, int64_t grid, cudaStream_t s,
+                                 bool pdl) {
+    if (noise && pl) return launch_one<S, true, true, FLIPS>(a, block, grid, s, pdl);
+    if (noise) return launch_one<S, true, false, FLIPS>(a, block, grid, s, pdl);
+    if (pl) return launch_one<S, false, true, FLIPS>(a, block, grid, s, pdl);
+    return launch_one<S, false, false, FLIPS>(a, block, grid, s, pdl);
 }
 
 // The variant that writes the moments of nodes changing side runs the items
 // near particles (mode STREAM_NEAR, or STREAM_ALL when particles exist).
 template <class S>
-static cudaError_t launch_kind(bool noise, bool pl, const StreamArgs& a, int block, int64_t grid, cudaStream_t s) {
-    if (a.flips) return launch_kind_f<S, true>(noise, pl, a, block, grid, s);
-    return launch_kind_f<S, false>(noise, pl, a, block, grid, s);
+static cudaError_t launch_kind(bool noise, bool pl, const StreamArgs& a, int block, int64_t grid, cudaStream_t s,
+                               bool pdl) {
+    if (a.flips) return launch_kind_f<S, true>(noise, pl, a, block, grid, s, pdl);
+    return launch_kind_f<S, false>(noise, pl, a, block, grid, s, pdl);
 }
 
 cudaError_t launch_stream_staged(int kind, bool noise, bool pl, const StreamArgs& a, int block, int64_t grid,
                                  int stages, cudaStream_t s);
 
 cudaError_t launch_stream_collide(int kind, bool noise, bool pl, const StreamArgs& a, int block, int64_t grid,
-                                  int stages, cudaStream_t s) {
+                                  int stages, cudaStream_t s, bool pdl) {
     if (stages > 0 && a.mode != STREAM_NEAR) return launch_stream_staged(kind, noise, pl, a, block, grid, stages, s);
     switch (kind) {
-        case 0: return launch_kind<StF64>(noise, pl, a, block, grid, s);
-        case 1: return launch_kind<StF32>(noise, pl, a, block, grid, s);
-        case 2: return launch_kind<StF32S>(noise, pl, a, block, grid, s);
-        case 3: return launch_kind<StF16S>(noise, pl, a, block, grid, s);
-        case 4: return launch_kind<StBF16S>(noise, pl, a, block, grid, s);
+        case 0: return launch_kind<StF64>(noise, pl, a, block, grid, s, pdl);
+        case 1: return launch_kind<StF32>(noise, pl, a, block, grid, s, pdl);
+        case 2: return launch_kind<StF32S>(noise, pl, a, block, grid, s, pdl);
+        case 3: return launch_kind<StF16S>(noise, pl, a, block, grid, s, pdl);
+        case 4: return launch_kind<StBF16S>(noise, pl, a, block, grid, s, pdl);
         default: return cudaErrorInvalidValue;
     }
 }

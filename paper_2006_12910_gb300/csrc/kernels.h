@@ -46,9 +46,13 @@ enum { STREAM_ALL = 0, STREAM_FAR = 1, STREAM_NEAR = 2 };
 // stages == 0: the register-pipelined kernel (every mode).  stages >= 1 with
 // mode ALL or FAR: the staged kernel, in which each warp keeps `stages` row
 // segments in flight through bulk asynchronous copies into shared memory;
-// mode NEAR always takes the register kernel.
+// mode NEAR always takes the register kernel.  pdl: launch the register
+// kernel as a programmatic dependent of the kernel before it in stream s
+// (it is then placed on the SMs while that kernel drains, and waits for its
+// completion and memory flush before touching memory); ignored by the
+// staged kernel.
 cudaError_t launch_stream_collide(int kind, bool noise, bool pl, const StreamArgs& a, int block, int64_t grid,
-                                  int stages, cudaStream_t s);
+                                  int stages, cudaStream_t s, bool pdl = false);
 int store_vector_width(int kind);
 // CTAs of the register kernel (no flip moments) that fit on one SM at `block`
 // threads, for the storage kind and collision variant (0 on error).
@@ -141,7 +145,10 @@ constexpr int PL_STEP_LJ = PL_LJ | PL_ADVANCE | PL_AHEAD;
 // (rasterisation and marks of t+1), PL_LJ (Eq. MP2 at t) and
 // PL_LJ | PL_ADVANCE (Eq. MP2 at t+1)
 constexpr int PL_SETUP_R = PL_RASTER | PL_MARK | PL_ADVANCE;
-cudaError_t launch_particle_step(int kind, const PartArgs& a, int modes, cudaStream_t s);
+// pdl as for launch_stream_collide.  The launch of role A signals its
+// programmatic dependents once the particle states are solved, so that the
+// stream-collide pass after it is placed while the exchange completes.
+cudaError_t launch_particle_step(int kind, const PartArgs& a, int modes, cudaStream_t s, bool pdl = false);
 
 // The thread's message for lbm_last_error(NULL) (capi.cu).
 void set_global_error(const char* msg);

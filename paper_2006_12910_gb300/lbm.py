@@ -23,12 +23,14 @@ DIAG_N = 13
 
 EXPORTED = [
     "lbm_create", "lbm_create_ensemble", "lbm_set_geometry", "lbm_add_particles", "lbm_set_populations",
-    "lbm_get_populations", "lbm_step", "lbm_sync", "lbm_moments", "lbm_moments_device", "lbm_moments_async",
+    "lbm_get_populations", "lbm_step", "lbm_prepare_steps", "lbm_sync", "lbm_moments", "lbm_moments_device", "lbm_moments_async",
     "lbm_moments_async_wait", "lbm_particles", "lbm_particle_forces", "lbm_checks", "lbm_step_count",
     "lbm_save", "lbm_load", "lbm_autotune", "lbm_set_launch", "lbm_get_launch", "lbm_profile_steps", "lbm_time_stream", "lbm_fp64_fma_rate",
     "lbm_checks_noalloc", "lbm_set_wait_limit", "lbm_debug_fail_alloc", "lbm_last_error", "lbm_destroy",
 ]
 NOALLOC_MAX_ROWS = 16384
+PREPARE_MAX_STEPS = 256  # LBM_PREPARE_MAX_STEPS
+PREPARE_SLOTS = 4        # LBM_PREPARE_SLOTS
 
 
 class LbmError(RuntimeError):
@@ -93,6 +95,7 @@ def load(build_if_missing: bool = True):
             "lbm_set_populations": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
             "lbm_get_populations": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
             "lbm_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
+            "lbm_prepare_steps": (ctypes.c_int, [_vp, ctypes.c_int64]),
             "lbm_sync": (ctypes.c_int, [_vp]),
             "lbm_moments": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
             "lbm_moments_device": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
@@ -224,6 +227,10 @@ class Context:
 
     def step(self, n=1):
         self._ck(self.L.lbm_step(self.h, int(n)))
+
+    def prepare_steps(self, n):
+        """lbm_prepare_steps: build the step graphs of exactly n steps now (blocking)."""
+        self._ck(self.L.lbm_prepare_steps(self.h, int(n)))
 
     def sync(self):
         self._ck(self.L.lbm_sync(self.h))

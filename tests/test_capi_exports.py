@@ -23,6 +23,15 @@ def test_every_declared_symbol_is_exported():
     assert sorted(lbm.EXPORTED) == declared
 
 
+def test_header_constants_match_the_binding():
+    from paper_2006_12910_gb300 import lbm
+    with open(os.path.join(ROOT, "include", "lbm.h")) as fh:
+        txt = fh.read()
+    defs = dict(re.findall(r"#define\s+(LBM_[A-Z_]+)\s+(\d+)", txt))
+    assert int(defs["LBM_PREPARE_MAX_STEPS"]) == lbm.PREPARE_MAX_STEPS
+    assert int(defs["LBM_PREPARE_SLOTS"]) == lbm.PREPARE_SLOTS
+
+
 def test_param_struct_layout_matches_header():
     from paper_2006_12910_gb300 import lbm
     # 6 int32, 6 double, kT, seed, domain_id + power_law, 6 doubles, store + max_particles, store_scale,
@@ -45,6 +54,7 @@ def test_invalid_parameters_rejected_without_gpu():
         assert h.value is None
         assert L.lbm_last_error(None)
     assert L.lbm_step(None, 1) == -1
+    assert L.lbm_prepare_steps(None, 20) == -1
     assert L.lbm_step_count(None) == -1
     assert L.lbm_set_launch(None, 2, 128, 2) == -1
     assert L.lbm_get_launch(None, None) == -1
