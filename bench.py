@@ -683,23 +683,53 @@ def main():
     # the particle state back to the host; finally read the moment fields back.
     e2e = None
     if rank == 0 or world > 1:
+        # End to end through the C ABI with host buffers: upload of the FP64 state from
+        # pinned memory, K steps whose particle states are written to a pinned host
+        # trajectory buffer at every step (lbm_record_particles) and read by the host after
+        # each call of `chunk` steps, the moments read back at the end.
         ctx2 = make_ctx(args.store)
         f0 = torch.empty((9, w.ny, w.nx), dtype=torch.float64, pin_memory=True)
         f0.numpy()[:] = ctx2.populations()
         K2 = args.e2e_steps
+        chunk = min(args.steps, K2, lbm.PREPARE_MAX_STEPS)
+        npart = len(w.particles)
+        rec = torch.empty((chunk, ctx2.particle_slots, 6), dtype=torch.float64, pin_memory=True)
+        ctx2.record_particles(rec)
+        ctx2.prepare_steps(chunk)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx2.set_populations(f0.numpy())
-        for _ in range(K2):
-            ctx2.step(1)
-            ctx2.particles_array()
+        done, umax = 0, 0.0
+        while done < K2:
+            n = min(chunk, K2 - done)
+            ctx2.step(n)
+            ctx2.sync()
+            r = rec.numpy()
+            umax = max(umax, float(np.abs(r[:, :npart, 2:4]).max()))  # every step's particle velocities
+            done += n
         rho, ux, uy = ctx2.moments()
         t = time.perf_counter() - t0
+        ctx2.record_particles(None)
         h2d = 9 * nodes * 8 / K2
-        d2h = len(w.particles) * 64 + 3 * nodes * 8 / K2
+        d2h = npart * 48 + 3 * nodes * 8 / K2
         e2e = {"value": world * nodes * K2 / t / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": K2,
-               "what": "lbm_set_populations(pinned FP64) + K x [lbm_step(1) + lbm_particles (particles_array)] + lbm_moments"}
+               "d2h_bytes_per_step": d2h, "steps": K2, "max_particle_speed": umax,
+               "what": (f"lbm_set_populations(pinned FP64) + K/{chunk} x [lbm_step({chunk}) with every step's "
+                        "particle states written to pinned host memory (lbm_record_particles) + lbm_sync + host "
+                        "read of the records] + lbm_moments")}
+        # the same with a blocking particle read after every single step
+        K3 = min(K2, 500)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx2.set_populations(f0.numpy())
+        for _ in range(K3):
+            ctx2.step(1)
+            ctx2.particles_array()
+        ctx2.moments()
+        t3 = time.perf_counter() - t0
+        e2e["blocking_read_each_step"] = {
+            "value": world * nodes * K3 / t3 / 1e6, "unit": UNIT, "steps": K3,
+            "what": "lbm_set_populations + K x [lbm_step(1) + lbm_particles] + lbm_moments"}
         ctx2.close()
 
     # ---- other storage kinds on the same workload (short) ----------------------------------

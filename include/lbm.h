@@ -140,6 +140,24 @@ int lbm_get_populations(lbm_ctx* ctx, int dom, double* f);
  * returns without waiting. */
 int lbm_step(lbm_ctx* ctx, int64_t nsteps);
 
+/* Per-step particle trajectories without a host round trip per step (the
+ * particle velocity and position series behind the Brownian statistics of
+ * Sec. 6; no paper counterpart as an interface).  While a buffer is set,
+ * every step writes the state of every particle after it, from the particle
+ * force launch directly into host_buf (page-locked host memory mapped into
+ * the device address space: cudaHostAlloc, or cudaHostRegister with the
+ * mapped flag), as record (t mod capacity) for the step count t it reaches:
+ * np_slots x 6 doubles (x, y, U, V, Omega, theta), np_slots the sum of
+ * max_particles over the domains, domain d's particles from the sum of
+ * max_particles of the domains before it; slots beyond a domain's particle
+ * count are not written.  A record is complete once a blocking call
+ * (lbm_sync, lbm_particles, ...) issued after the step has returned.  The
+ * caller keeps the buffer alive and page-locked while it is set;
+ * host_buf = NULL stops recording.  Waits for the queued steps; the step
+ * graphs are rebuilt at the next step.  LBM_E_INVAL for memory that is not
+ * page-locked and mapped, or capacity < 1. */
+int lbm_record_particles(lbm_ctx* ctx, double* host_buf, int64_t capacity);
+
 /* Set-up for a step count the caller repeats (no paper counterpart): build
  * the step graphs of exactly nsteps steps (1 .. LBM_PREPARE_MAX_STEPS) from
  * either state parity now, so that every later lbm_step(nsteps) replays one

@@ -674,7 +674,10 @@ __global__ void __launch_bounds__(LO >= 2 ? BC_BLOCK : PBLOCK) k_particle_step(P
                     xm[0] = xm[1] = xm[2] = 0.0;
                 }
             }
-            if (advance) a.state[(int64_t)(par ^ 1) * a.np + p] = n;
+            if (advance) {
+                a.state[(int64_t)(par ^ 1) * a.np + p] = n;
+                if (a.rec) a.rec[((t + 1) % a.rec_cap) * a.np + p] = n;
+            }
 #pragma unroll
             for (int c = 0; c < 6; ++c) zsh[c] = z[c];
             f0sh[0] = F0x;

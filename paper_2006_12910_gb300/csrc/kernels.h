@@ -130,6 +130,11 @@ struct PartArgs {
     const double2* ljwall;     // per node: Eq. MP2 force from static solid / wall nodes within r_it (or null)
     const LjEntry* lj_tab;     // [ndom][LJ_TAB], valid entries first
     const int32_t* lj_cnt;     // [ndom]
+    // Trajectory records (or null): the force launch that reaches step t + 1
+    // also writes each particle's new state to rec[((t + 1) % rec_cap) * np + p],
+    // page-locked host memory mapped into the device address space.
+    PartState* rec;
+    int64_t rec_cap;
 };
 // Particle-step modes: forces + Newton-Euler, exchange of the link slots,
 // advance to t+1, rebuild of the link / flip lists, marking of the near items,

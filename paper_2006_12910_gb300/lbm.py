@@ -23,7 +23,7 @@ DIAG_N = 13
 
 EXPORTED = [
     "lbm_create", "lbm_create_ensemble", "lbm_set_geometry", "lbm_add_particles", "lbm_set_populations",
-    "lbm_get_populations", "lbm_step", "lbm_prepare_steps", "lbm_sync", "lbm_moments", "lbm_moments_device", "lbm_moments_async",
+    "lbm_get_populations", "lbm_step", "lbm_prepare_steps", "lbm_record_particles", "lbm_sync", "lbm_moments", "lbm_moments_device", "lbm_moments_async",
     "lbm_moments_async_wait", "lbm_particles", "lbm_particle_forces", "lbm_checks", "lbm_step_count",
     "lbm_save", "lbm_load", "lbm_autotune", "lbm_set_launch", "lbm_get_launch", "lbm_profile_steps", "lbm_time_stream", "lbm_fp64_fma_rate",
     "lbm_checks_noalloc", "lbm_set_wait_limit", "lbm_debug_fail_alloc", "lbm_last_error", "lbm_destroy",
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
             "lbm_get_populations": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
             "lbm_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
             "lbm_prepare_steps": (ctypes.c_int, [_vp, ctypes.c_int64]),
+            "lbm_record_particles": (ctypes.c_int, [_vp, _vp, ctypes.c_int64]),
             "lbm_sync": (ctypes.c_int, [_vp]),
             "lbm_moments": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp]),
             "lbm_moments_device": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
@@ -281,6 +282,22 @@ class Context:
         arr, view, cap = buf
         n = self._ck(self.L.lbm_particles(self.h, dom, arr, cap))
         return view[:n, :8].copy()
+
+    def record_particles(self, buf, capacity=None):
+        """lbm_record_particles: per-step particle states into `buf`, a page-locked float64
+        host tensor (torch.empty(..., pin_memory=True)) of capacity x np_slots x 6 values
+        (x, y, U, V, Omega, theta); None stops recording.  Record (t mod capacity) holds the
+        states after step t."""
+        if buf is None:
+            self._ck(self.L.lbm_record_particles(self.h, None, 0))
+            return
+        cap = int(capacity if capacity is not None else buf.shape[0])
+        self._ck(self.L.lbm_record_particles(self.h, ctypes.c_void_p(buf.data_ptr()), cap))
+
+    @property
+    def particle_slots(self):
+        """Particle slots of the context (sum of max_particles over the domains)."""
+        return sum(int(p.max_particles) for p in self.params)
 
     def particle_forces(self, i, dom=0):
         out = np.zeros(DIAG_N)

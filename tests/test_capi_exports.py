@@ -55,6 +55,7 @@ def test_invalid_parameters_rejected_without_gpu():
         assert L.lbm_last_error(None)
     assert L.lbm_step(None, 1) == -1
     assert L.lbm_prepare_steps(None, 20) == -1
+    assert L.lbm_record_particles(None, None, 4) == -1
     assert L.lbm_step_count(None) == -1
     assert L.lbm_set_launch(None, 2, 128, 2) == -1
     assert L.lbm_get_launch(None, None) == -1

@@ -70,3 +70,51 @@ def test_prepare_rejects_counts_out_of_range():
     ctx.step(2)
     ctx.sync()
     ctx.close()
+
+
+def test_recorded_trajectories_equal_the_states_read_step_by_step():
+    torch = pytest.importorskip("torch")
+    w = workloads.porous(384, 192, n_obstacles=600, n_particles=120)
+    f0 = workloads.random_populations(w.nx, w.ny, seed=78, amp=0.005, solid=w.solid)
+    a, b = _ctx(w, f0), _ctx(w, f0)
+    ns, cap = a.particle_slots, 8
+    buf = torch.full((cap, ns, 6), float("nan"), dtype=torch.float64, pin_memory=True)
+    a.record_particles(buf)
+    a.prepare_steps(20)
+    a.step(3)
+    a.step(20)  # steps 4 .. 23: records of steps 16 .. 23 remain, at slots (t mod 8)
+    a.sync()
+    rec = buf.numpy().copy()
+    seen = {}
+    for t in range(1, 24):
+        b.step(1)
+        seen[t] = b.particles_array()
+    for t in range(16, 24):
+        want = seen[t][:, [0, 1, 4, 5, 6, 7]]  # x, y, U, V, Omega, theta
+        assert np.array_equal(rec[t % cap, :len(want)], want), t
+    assert np.isnan(rec[:, len(w.particles):]).all()  # slots beyond the particle count stay untouched
+    # stop recording: later steps leave the buffer alone
+    a.record_particles(None)
+    before = buf.numpy().copy()
+    a.step(5)
+    a.sync()
+    assert np.array_equal(buf.numpy(), before, equal_nan=True)
+    a.close()
+    b.close()
+
+
+def test_record_rejects_pageable_memory_and_bad_capacity():
+    torch = pytest.importorskip("torch")
+    w = workloads.porous(256, 128, n_obstacles=100, n_particles=10)
+    ctx = _ctx(w, workloads.random_populations(w.nx, w.ny, seed=6, amp=0.005, solid=w.solid))
+    pageable = torch.zeros((4, ctx.particle_slots, 6), dtype=torch.float64)
+    with pytest.raises(lbm.LbmError):
+        ctx.record_particles(pageable)
+    pinned = torch.zeros((4, ctx.particle_slots, 6), dtype=torch.float64, pin_memory=True)
+    with pytest.raises(lbm.LbmError):
+        ctx.record_particles(pinned, capacity=0)
+    ctx.record_particles(pinned)
+    ctx.step(4)
+    ctx.sync()
+    assert np.abs(pinned.numpy()[:, :1]).sum() > 0
+    ctx.close()
