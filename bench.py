@@ -876,7 +876,10 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                            "l2": "no flush; per-step footprint (2 arenas) exceeds the 129 MB L2",
                            "launch": {"kernel": k1_name, "block": launch[1], "stages": launch[2],
-                                      "grid": launch[3], "graph_steps": 8}},
+                                      "grid": launch[3],
+                                      "graphs": ("one prepared graph of the timed step count"
+                                                 if args.steps <= lbm.PREPARE_MAX_STEPS
+                                                 else "graphs of 2^j steps, one per binary digit of the count")}},
                 "fluid_node_mlups": value * fluid / nodes,
                 "clocks": clk, "gpu_launches": args.steps * kernels_per_step,
                 "roofline": roofline, "e2e": e2e,

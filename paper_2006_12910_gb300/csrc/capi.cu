@@ -722,17 +722,17 @@ int lbm_create_ensemble(int ndom, const lbm_params* per_domain, void* cuda_strea
     {
         int lo = 0, hi = 0;
         CKCR(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-        // Priorities of the overlapped step's chains: the force launch and NEAR
-        // pass (the particle chain) and the rasterisation for the next step
-        // highest; the FAR pass, which bounds the step, in the middle; the
-        // Eq. MP2 sums, needed only two steps later, lowest, so that their CTAs
-        // fill the SMs only where no FAR CTA is waiting (measured 35.7 -> 34.0
-        // us per step on the porous workload against all particle streams
-        // highest and the FAR pass lowest).
+        // Priorities of the overlapped step's chains: every particle launch
+        // highest, the FAR pass lowest.  (The Eq. MP2 sums are needed only two
+        // steps later, but below the FAR pass, or with the FAR pass in the
+        // middle, they starve once the particles come near obstacles and the
+        // sums do real work: 42.6 or 38.2 us per step over 20,000 steps of the
+        // porous workload against 36.2 with this order, although they were
+        // 1.5 us faster while the particles were still far from everything.)
         CKCR(cudaStreamCreateWithPriority(&c->cap_stream, cudaStreamNonBlocking, hi));
-        CKCR(cudaStreamCreateWithPriority(&c->far_stream, cudaStreamNonBlocking, (lo + hi) / 2));
+        CKCR(cudaStreamCreateWithPriority(&c->far_stream, cudaStreamNonBlocking, lo));
         CKCR(cudaStreamCreateWithPriority(&c->rast_stream, cudaStreamNonBlocking, hi));
-        CKCR(cudaStreamCreateWithPriority(&c->lj_stream, cudaStreamNonBlocking, lo));
+        CKCR(cudaStreamCreateWithPriority(&c->lj_stream, cudaStreamNonBlocking, hi));
     }
     CKCR(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     CKCR(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
